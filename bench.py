@@ -1,0 +1,293 @@
+"""Benchmark of the generic-mode data-sharing runtime on one GB300 (or N,
+one process per GPU, each running its own independent regions).
+
+Default workload: the wide plain-launch configuration -- 1024 teams x 256
+threads, 3 nested levels each pushing a 1088-byte frame (16 int32 scalars
++ int32[256]), 4M int32 output -- one region instance per step, launched
+through the C ABI. Metric: regions/s, with push+pop/s beside it.
+
+Prints ONE JSON line (rank 0). `--impl reference` times the CPU oracle on
+the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), source="measured")
+    return dict(hbm_gbs=6800.0, source="fallback")
+
+
+# ---------------------------------------------------------------------------
+# Workloads
+# ---------------------------------------------------------------------------
+def make_workload(name: str, rank: int = 0):
+    seed = wl.DEFAULT_SEED + 7919 * rank
+    if name == "nested":
+        work = wl.nested(teams=1024, threads=256, depth=3, elems_per_team=4096, seed=seed)
+        r = work.regions[0]
+        algo_bytes = (r.teams * r.depth * 1088          # images read
+                      + 4 * r.teams * r.param           # output written
+                      + 32 * r.teams)                   # team statuses written
+        cfg = dict(workload="nested_1024x256_d3", teams=1024, threads=256, depth=3,
+                   frame_bytes=1088, out_elems=1024 * 4096, slab_bytes=3264)
+        return work, 3264, 0, algo_bytes, cfg
+    raise SystemExit("unknown workload %r" % name)
+
+
+# ---------------------------------------------------------------------------
+# Clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return dict(sm_mhz=statistics.median(sm) if sm else None,
+                    sm_max_mhz=max(mx) if mx else None, reasons=reasons, samples=len(rows))
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded sample of the same workload)
+# ---------------------------------------------------------------------------
+def time_oracle(work, slab, ovf, budget_s: float = 10.0):
+    import oracle
+    oracle.build()
+    r = work.regions[0]
+    out = np.zeros(work.out_bytes // 4, dtype=np.int32)
+    st = np.zeros(work.n_status, dtype=oracle.STATUS_DTYPE)
+    teams_done = 0
+    t0 = time.perf_counter()
+    chunk = 64
+    while time.perf_counter() - t0 < budget_s:
+        b = teams_done % r.teams
+        e = min(b + chunk, r.teams)
+        oracle.run_region(r, work.images, out, st, slab, ovf, b, e)
+        teams_done += e - b
+    dt = time.perf_counter() - t0
+    regions = teams_done / r.teams
+    return dict(value=regions / dt, unit="regions/s", cores=1, kind="oracle",
+                sample="%d teams of the workload (%.2f regions) in %.1f s, one thread"
+                       % (teams_done, regions, dt))
+
+
+# ---------------------------------------------------------------------------
+# Main
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="dsr", choices=["dsr", "reference"])
+    ap.add_argument("--workload", default="nested")
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        work, slab, ovf, algo_bytes, cfg = make_workload(args.workload, 0)
+        for _ in range(args.warmup):
+            pass
+        per_step = []
+        budget = max(1.0, 60.0 / max(args.steps, 1))
+        samples = []
+        for _ in range(args.steps):
+            s = time_oracle(work, slab, ovf, budget_s=budget)
+            samples.append(s)
+            per_step.append(s["value"])
+        v = float(statistics.median(per_step))
+        line = dict(impl="reference", metric="regions/s", value=v, unit="regions/s",
+                    n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                    ms_per_step=1000.0 / v, higher_is_better=True, scaling="weak",
+                    vs_baseline=None, dtype="int32", data="synthetic", config=cfg,
+                    e2e=dict(value=v, unit="regions/s", h2d_bytes_per_step=0,
+                             d2h_bytes_per_step=0),
+                    cpu_baseline=dict(value=v, unit="regions/s", cores=1, kind="oracle",
+                                      sample=samples[-1]["sample"]))
+        print(json.dumps(line))
+        return
+
+    import torch
+    import paper_1711_10413_gb300 as dsr
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dsr.build()
+
+    work, slab, ovf, algo_bytes, cfg = make_workload(args.workload, rank)
+    region = work.regions[0]
+    rt = dsr.Runtime(local, slab_bytes=slab, overflow_bytes_per_team=ovf,
+                     max_teams=region.teams if ovf else 0)
+    images, out, status = rt.device_buffers(work)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        dsr.dsr_launch_region(rt.ctx, region, images, out, status, stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i)           # L2 flush between steps, outside the events
+        starts[i].record(stream)
+        step()
+        stops[i].record(stream)
+    torch.cuda.synchronize()
+    bracket_s = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in zip(starts, stops)]
+    ms_step = float(np.mean(ms))
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+
+    # parity spot check of the timed buffers (full output vs the oracle)
+    status_np = status.cpu().numpy().view(dsr.TEAM_STATUS_DTYPE)
+    bad_status = int((status_np["status"] != 0).sum() + (status_np["depth_final"] != 0).sum())
+
+    # e2e: the same region from pinned host memory through the C ABI
+    img_h = torch.from_numpy(np.ascontiguousarray(work.images)).pin_memory()
+    out_h = torch.empty(out.numel(), dtype=torch.int32).pin_memory()
+    st_h = torch.empty(status.numel(), dtype=torch.int32).pin_memory()
+    ib, ob, _ = dsr.dsr_region_extent(region)
+
+    def e2e_step():
+        dsr.dsr_run_region_host(rt.ctx, region, img_h, ib, out_h, ob, st_h, images, out,
+                                status, stream)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t1) / args.steps
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peaks = _peaks()
+    regions_per_s = world * 1000.0 / ms_step
+    achieved = algo_bytes / (ms_step * 1e-3) / 1e9
+    line = dict(
+        metric="regions/s", value=regions_per_s, unit="regions/s", n_gpus=world,
+        steps=args.steps, warmup=args.warmup, ms_per_step=ms_step, higher_is_better=True,
+        scaling="weak", vs_baseline=None, dtype="int32", data="synthetic",
+        config=dict(cfg, parallelism="independent regions per GPU" if world > 1 else "1 GPU",
+                    l2="flushed between steps (256 MiB write, outside the timed events)"),
+        push_pop_per_s=regions_per_s * region.teams * region.depth,
+        roofline=dict(bound="hbm", achieved=achieved, peak=peaks["hbm_gbs"], unit="GB/s",
+                      frac=achieved / peaks["hbm_gbs"], traffic=None,
+                      peak_source=peaks["source"], algorithmic_bytes=algo_bytes),
+        e2e=dict(value=world / e2e_s, unit="regions/s", h2d_bytes_per_step=int(ib),
+                 d2h_bytes_per_step=int(ob + 32 * region.teams)),
+        gpu_launches=args.steps,
+        bracket_ms_per_step=1000.0 * bracket_s / args.steps,
+        bad_team_status=bad_status,
+        clocks=clk,
+    )
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = time_oracle(work, slab, ovf, budget_s=args.cpu_budget)
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * dsr.h -- C ABI of the GB300 data-sharing runtime for OpenMP-style
+ * generic-mode target regions.
+ *
+ * The method (Bercea et al., "Implementing implicit OpenMP data sharing on
+ * GPUs", LLVM-HPC'17): in generic mode one master thread per team runs the
+ * sequential code of a target region while the worker threads wait
+ * (Sec. 4, Fig. "codegen-master" / "codegen-worker"); locals declared in
+ * that code and referenced by a nested parallel region are implicitly
+ * shared (Sec. 3.2). They live on a per-team stack in shared memory
+ * (Sec. 5.3, "Shared memory stack"), the master passes the workers
+ * references to them (Sec. 5.1-5.2), and a global-memory fallback catches
+ * what does not fit (Sec. 5.2, last paragraph; Sec. 7).
+ *
+ * This library implements that runtime on sm_103a: a per-team frame stack
+ * in a shared-memory slab spilling to per-team global overflow slabs, a
+ * master/worker state machine with named-barrier handoff, frame-address
+ * publication and a region-body executor. It runs built-in region programs
+ * (DSR_PROG_*), each a fixed master code + parallel bodies.
+ *
+ * Conventions for every entry point:
+ *  - Return value: a dsr_status (DSR_OK = 0). Failures never abort the
+ *    process; dsr_last_error_string() describes the last failure of a ctx.
+ *  - Pointers named *_dev are device pointers (e.g. a torch tensor's
+ *    data_ptr) owned by the caller; the library never frees them. Pointers
+ *    named *_host are host pointers owned by the caller.
+ *  - `stream` is a cudaStream_t passed as void* (0 = legacy default stream);
+ *    launches are asynchronous on it unless stated otherwise.
+ *  - Device-side errors (stack overflow, LIFO misuse) are written to the
+ *    per-team dsr_team_status records; the host reads them after a sync.
+ *    No kernel traps.
+ */
+#ifndef DSR_H_
+#define DSR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DSR_MAX_DEPTH 4      /* frame sizes one region descriptor carries */
+#define DSR_MAX_FRAMES 8     /* frame-table entries per team stack */
+#define DSR_MAX_THREADS 1024 /* threads per team, master warp included */
+
+typedef enum dsr_status {
+  DSR_OK = 0,
+  DSR_ERR_INVALID = 1,  /* malformed argument or descriptor */
+  DSR_ERR_OVERFLOW = 2, /* a push did not fit in slab + overflow slab */
+  DSR_ERR_LIFO = 3,     /* a pop named a frame that is not the top one */
+  DSR_ERR_BUDGET = 4,   /* not enough pool / queue space for the request */
+  DSR_ERR_TIMEOUT = 5,  /* a bounded device-side wait ran out */
+  DSR_ERR_CUDA = 6      /* a CUDA runtime call failed */
+} dsr_status;
+
+/* Built-in region programs (the master code and parallel bodies each one
+ * runs are stated beside each id). W = threads - 32 workers; a region runs
+ * `width` threads (0 = all W; with W == 0 the master runs it alone). */
+enum {
+  /* Sec. 6.1, Fig. "Implicitly sharing 8 variables": shares param ints and
+   * the array reference; a[team*width + tid] += sum of the ints (c_i = i). */
+  DSR_PROG_PAPER_SCALARS = 1,
+  /* Sec. 6.1, Fig. "Implicitly sharing an array": shares param int[width]
+   * arrays filled with 10; a[team*width + tid] += sum_m d_m[tid]. */
+  DSR_PROG_PAPER_ARRAYS = 2,
+  /* param sequential regions per team, each pushing int32 s[4] from the
+   * image; out[(r*teams + team)*width + tid] =
+   *   (s0*tid + s1) ^ ((s2 >> (tid & 7)) + s3). */
+  DSR_PROG_SCALARS = 3,
+  /* depth nested master-side calls, each pushing {int32 s[16]; int32
+   * arr[256]} (1088 B) from a per-(team, level) image; the innermost level
+   * writes param int32 per team; chk[k] = the word the master summed after
+   * level k's join. */
+  DSR_PROG_NESTED = 4,
+  /* one frame of float[frame_bytes/4] from a per-team image; out[team*width
+   * + tid] = fp32 sum, in index order, of the elements tid, tid+width, ... */
+  DSR_PROG_SWEEP = 5,
+  /* heterogeneous instances: depth levels of int32[frame_bytes[k]/4] from
+   * per-instance images; innermost out[team*width + tid] = hash-sum of the
+   * worker's strided elements of every live frame. */
+  DSR_PROG_HETERO = 6
+};
+
+/* One region instance: a target region with `teams` teams (one CTA each in
+ * the plain launch), Sec. 4 and Sec. 6.1. 64 bytes, little-endian. */
+typedef struct dsr_region_desc {
+  uint32_t program;                    /* DSR_PROG_* */
+  uint32_t teams;                      /* >= 1 */
+  uint32_t threads;                    /* per team, multiple of 32 in [32, 1024] */
+  uint32_t depth;                      /* frames pushed per team, 1..DSR_MAX_DEPTH */
+  uint32_t frame_bytes[DSR_MAX_DEPTH]; /* size of frame k, multiple of 4 */
+  uint32_t width;                      /* threads per parallel region, 0 = all */
+  uint32_t param;                      /* program parameter (see DSR_PROG_*) */
+  uint32_t salt;                       /* per-instance salt (DSR_PROG_HETERO) */
+  uint32_t status_index;               /* team 0's entry in the status array */
+  uint64_t image_offset;               /* byte offset of the images, 16-aligned */
+  uint64_t out_offset;                 /* byte offset of the output, 16-aligned */
+} dsr_region_desc;
+
+/* What each team reports when it ends (32 bytes). */
+typedef struct dsr_team_status {
+  int32_t status;              /* DSR_OK, DSR_ERR_OVERFLOW or DSR_ERR_LIFO */
+  uint32_t depth_final;        /* live frames at team exit: 0 when balanced */
+  uint32_t hwm_bytes;          /* peak reserved stack bytes, slab + overflow */
+  uint32_t spill_bytes;        /* peak reserved overflow-slab bytes */
+  uint32_t chk[DSR_MAX_DEPTH]; /* program check words (worker->master writes) */
+} dsr_team_status;
+
+typedef struct dsr_config {
+  int32_t device;           /* CUDA device ordinal */
+  uint32_t flags;           /* reserved, 0 */
+  uint64_t wait_timeout_ns; /* bound on every device-side wait; 0 = 1 s */
+} dsr_config;
+
+/* Shared-memory and occupancy figures of a team shape on this GPU, the
+ * GB300 counterpart of the paper's per-team footprint (Sec. 6.2.1: stack +
+ * reference list + thread-private state) and teams-per-SM arithmetic
+ * (Sec. 6.2.2). */
+typedef struct dsr_footprint {
+  uint32_t smem_per_team;   /* dynamic smem: control block + frame slab */
+  uint32_t ctrl_bytes;      /* control block: frame table, work, counters */
+  uint32_t slab_bytes;      /* frame slab */
+  uint32_t teams_per_sm;    /* resident teams per SM (model) */
+  uint32_t limit;           /* 1 = threads, 2 = smem, 3 = registers, 4 = blocks */
+  uint32_t spill_bytes;     /* bytes per team that go to the overflow slab */
+} dsr_footprint;
+
+typedef struct dsr_ctx dsr_ctx;
+
+/* ---- lifecycle ---------------------------------------------------------- */
+
+/* Create a context on cfg->device (NULL cfg: device 0, defaults). Allocates
+ * only host metadata. *out receives the handle, owned by the caller and
+ * released with dsr_destroy. Errors: DSR_ERR_INVALID (out == NULL),
+ * DSR_ERR_CUDA (device not usable). */
+int32_t dsr_create(dsr_ctx **out, const dsr_config *cfg);
+
+/* Release a context and the CUDA graphs it captured. Caller-owned buffers
+ * are untouched. NULL is accepted. */
+int32_t dsr_destroy(dsr_ctx *ctx);
+
+/* Text of the ctx's last failure ("" if none). Owned by the ctx; valid until
+ * the next call on it. Accepts NULL (returns the process-wide last error). */
+const char *dsr_last_error_string(const dsr_ctx *ctx);
+
+/* ---- stacks (Sec. 5.3 shared stack, Sec. 5.2 global fallback) ---------- */
+
+/* Configure every team's stack: a shared-memory slab of smem_slab_bytes
+ * (multiple of 16, at most what one CTA can hold next to the control
+ * block) and a global overflow slab of overflow_bytes_per_team, carved for
+ * team t at overflow_pool_dev + t * overflow_bytes_per_team. The pool is a
+ * caller-owned device buffer of pool_bytes (16-byte aligned) that the ctx
+ * borrows; max_teams * overflow_bytes_per_team must fit in it. A push that
+ * fits in neither slab fails with DSR_ERR_OVERFLOW in the team's status.
+ * Errors: DSR_ERR_INVALID (sizes, alignment), DSR_ERR_BUDGET (pool too
+ * small). */
+int32_t dsr_stack_init(dsr_ctx *ctx, uint32_t smem_slab_bytes, uint64_t overflow_bytes_per_team,
+                       uint32_t max_teams, void *overflow_pool_dev, uint64_t pool_bytes);
+
+/* ---- host-side checks (no GPU needed) ---------------------------------- */
+
+/* Check a descriptor: shape limits, the frame sizes its program requires,
+ * 16-byte alignment of offsets, and that its images, outputs and statuses
+ * fit in image_bytes, out_bytes and n_status. DSR_OK or DSR_ERR_INVALID. */
+int32_t dsr_validate_region(const dsr_region_desc *d, uint64_t image_bytes, uint64_t out_bytes,
+                            uint64_t n_status);
+
+/* Bytes of input image, output and status entries a descriptor needs
+ * (any pointer may be NULL). DSR_ERR_INVALID for a malformed descriptor. */
+int32_t dsr_region_extent(const dsr_region_desc *d, uint64_t *image_bytes, uint64_t *out_bytes,
+                          uint64_t *n_status);
+
+/* Footprint and occupancy model of a team shape (threads, frame sizes of
+ * one descriptor, slab size) on a GB300-class SM: 228 KB shared memory per
+ * SM with 1 KB reserved per CTA, 64 warps, 32 CTAs, 65536 registers; regs is
+ * the kernel's registers per thread (0 = 64). No GPU is touched. */
+int32_t dsr_footprint_model(const dsr_region_desc *d, uint32_t slab_bytes, uint32_t regs,
+                            dsr_footprint *out);
+
+/* ---- plain launch: one CTA per team, one launch per region -------------- */
+
+/* Launch one region instance (Sec. 4: the target region is one kernel
+ * launch): d->teams CTAs of d->threads threads on `stream`, each with the
+ * ctx's slab. images_dev (image_bytes long) and out_dev (out_bytes long)
+ * are the buffers the descriptor's offsets index; status_dev holds n_status
+ * records, of which teams d->status_index .. + d->teams - 1 are written.
+ * The descriptor is checked against these sizes before anything launches.
+ * Requires dsr_stack_init; d->teams <= the max_teams given there when an
+ * overflow slab is configured. Asynchronous. Errors: DSR_ERR_INVALID,
+ * DSR_ERR_BUDGET, DSR_ERR_CUDA (launch failure). */
+int32_t dsr_launch_region(dsr_ctx *ctx, const dsr_region_desc *d, const void *images_dev,
+                          uint64_t image_bytes, void *out_dev, uint64_t out_bytes,
+                          dsr_team_status *status_dev, uint64_t n_status, void *stream);
+
+/* The same region from host memory: copies image_bytes from images_host to
+ * images_dev, launches, copies out_bytes of out_dev back to out_host and
+ * the statuses to status_host, then synchronises `stream`. Host buffers
+ * should be pinned for asynchronous copies. out_dev is first written from
+ * out_host when the program updates its output in place (PAPER_*). */
+int32_t dsr_run_region_host(dsr_ctx *ctx, const dsr_region_desc *d, const void *images_host,
+                            uint64_t image_bytes, void *out_host, uint64_t out_bytes,
+                            dsr_team_status *status_host, void *images_dev, void *out_dev,
+                            dsr_team_status *status_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DSR_H_ */

@@ -53,10 +53,21 @@ STATUS_DTYPE = np.dtype([("status", "<i4"), ("depth_final", "<u4"), ("hwm_bytes"
 assert STATUS_DTYPE.itemsize == 32 and ctypes.sizeof(Region) == 64
 
 
+def _foreign(path: str) -> bool:
+    """True when `path` was built for another CPU architecture."""
+    import sys
+
+    def machine(p):
+        with open(p, "rb") as f:
+            h = f.read(20)
+        return int.from_bytes(h[18:20], "little") if h[:4] == b"\x7fELF" else -1
+    return machine(path) != machine(sys.executable)
+
+
 def build(force: bool = False) -> str:
     """Compile dsr_oracle.c into liboracle.so (plain gcc, -O2)."""
     with _lock:
-        stale = (not os.path.exists(_LIB)
+        stale = (not os.path.exists(_LIB) or _foreign(_LIB)
                  or os.path.getmtime(_LIB) < os.path.getmtime(_SRC))
         if force or stale:
             tmp = _LIB + ".%d.tmp" % os.getpid()

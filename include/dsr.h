@@ -56,7 +56,8 @@ typedef enum dsr_status {
 
 /* Built-in region programs (the master code and parallel bodies each one
  * runs are stated beside each id). W = threads - 32 workers; a region runs
- * `width` threads (0 = all W; with W == 0 the master runs it alone). */
+ * `width` threads (0 = all W; a team with W == 0 runs each region with one
+ * thread, a team of one). */
 enum {
   /* Sec. 6.1, Fig. "Implicitly sharing 8 variables": shares param ints and
    * the array reference; a[team*width + tid] += sum of the ints (c_i = i). */
@@ -202,6 +203,75 @@ int32_t dsr_run_region_host(dsr_ctx *ctx, const dsr_region_desc *d, const void *
                             uint64_t image_bytes, void *out_host, uint64_t out_bytes,
                             dsr_team_status *status_host, void *images_dev, void *out_dev,
                             dsr_team_status *status_dev, void *stream);
+
+/* ---- batched launch: many instances, one persistent kernel -------------- */
+
+/* CTA shape of the persistent kernel. Teams of any width run on it: a region
+ * wider than the CTA's workers runs its threads round robin on them. */
+typedef struct dsr_batch_tuning {
+  uint32_t threads;     /* CTA threads, multiple of 32 in [64, 1024] (32 are the master warp) */
+  uint32_t slab_bytes;  /* shared-memory slab per CTA, multiple of 16 */
+  uint32_t ctas_per_sm; /* resident CTAs per SM; 0 = as many as fit */
+  uint32_t reserved;    /* 0 */
+} dsr_batch_tuning;
+
+/* Device workspace a batch of n instances with total_teams teams needs:
+ * task cursors, cost-class counters and the (instance, team) task list.
+ * Caller-owned, 16-byte aligned, reusable across launches of the batch. */
+uint64_t dsr_batch_workspace_bytes(uint32_t n, uint64_t total_teams);
+
+/* Host-side check of n host descriptors against the buffer sizes, and the
+ * sum of their teams. DSR_ERR_INVALID names the first bad descriptor. */
+int32_t dsr_batch_count(const dsr_region_desc *descs_host, uint32_t n, uint64_t image_bytes,
+                        uint64_t out_bytes, uint64_t n_status, uint64_t *total_teams);
+
+/* Run n region instances of one program (descs_dev: n descriptors in device
+ * memory, 16-byte aligned) in one persistent launch on `stream`: a grid of
+ * CTAs of tuning->threads threads with a slab of tuning->slab_bytes each
+ * (NULL tuning: 256 threads, 16 KB), pulling (instance, team) tasks from a
+ * cursor. This is the paper's fork/join runtime (Sec. 4, 5) run for many
+ * target regions at once instead of one kernel launch per region. Every
+ * descriptor is checked on the device before its teams run; a bad one (or
+ * one of another program) gets DSR_ERR_INVALID in its statuses where those
+ * are addressable, and is counted (dsr_batch_errors). total_teams must be
+ * the instances' team sum; the workspace must hold
+ * dsr_batch_workspace_bytes(n, total_teams). Overflow slabs come from the
+ * ctx's pool, one per CTA (the grid is capped at the pool's max_teams).
+ * use_graph != 0 captures the launch in a CUDA graph kept by the ctx
+ * (keyed by all arguments) and replays it. Asynchronous. Errors:
+ * DSR_ERR_INVALID, DSR_ERR_BUDGET (workspace too small), DSR_ERR_CUDA. */
+int32_t dsr_launch_batch(dsr_ctx *ctx, const dsr_region_desc *descs_dev, uint32_t n,
+                         uint32_t program, uint64_t total_teams, const void *images_dev,
+                         uint64_t image_bytes, void *out_dev, uint64_t out_bytes,
+                         dsr_team_status *status_dev, uint64_t n_status, void *workspace_dev,
+                         uint64_t workspace_bytes, const dsr_batch_tuning *tuning, void *stream,
+                         int use_graph);
+
+/* After a batch completed: tasks rejected on the device and tasks counted
+ * by its scan (synchronises `stream`). */
+int32_t dsr_batch_errors(dsr_ctx *ctx, const void *workspace_dev, uint32_t *errors,
+                         uint64_t *tasks_counted, void *stream);
+
+/* Autotuner: runs the batch once per candidate CTA shape (64..512
+ * threads) and slab size (2..64 KB), each at the most resident CTAs per SM
+ * that fit, and returns the fastest in *best (and its time in *best_ms).
+ * The outputs hold a correct result afterwards. Synchronises `stream`. The
+ * paper sizes its shared stack statically (Sec. 5.3, Sec. 7); this picks
+ * the slab from measured throughput instead. */
+int32_t dsr_autotune(dsr_ctx *ctx, const dsr_region_desc *descs_dev, uint32_t n,
+                     uint32_t program, uint64_t total_teams, const void *images_dev,
+                     uint64_t image_bytes, void *out_dev, uint64_t out_bytes,
+                     dsr_team_status *status_dev, uint64_t n_status, void *workspace_dev,
+                     uint64_t workspace_bytes, void *stream, dsr_batch_tuning *best,
+                     float *best_ms);
+
+/* One plain launch per region for n host descriptors: the per-region launch
+ * baseline of the batched form. Same checks and errors as
+ * dsr_launch_region. */
+int32_t dsr_launch_regions(dsr_ctx *ctx, const dsr_region_desc *descs_host, uint32_t n,
+                           const void *images_dev, uint64_t image_bytes, void *out_dev,
+                           uint64_t out_bytes, dsr_team_status *status_dev, uint64_t n_status,
+                           void *stream);
 
 #ifdef __cplusplus
 }

@@ -46,6 +46,11 @@ class dsr_config(ctypes.Structure):
                 ("wait_timeout_ns", ctypes.c_uint64)]
 
 
+class dsr_batch_tuning(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_uint32), ("slab_bytes", ctypes.c_uint32),
+                ("ctas_per_sm", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
 class dsr_footprint(ctypes.Structure):
     _fields_ = [("smem_per_team", ctypes.c_uint32), ("ctrl_bytes", ctypes.c_uint32),
                 ("slab_bytes", ctypes.c_uint32), ("teams_per_sm", ctypes.c_uint32),
@@ -88,6 +93,14 @@ def _declare(L):
                                      _vp]),
         "dsr_run_region_host": (_i32, [_vp, P(dsr_region_desc), _vp, _u64, _vp, _u64, _vp,
                                        _vp, _vp, _vp, _vp]),
+        "dsr_batch_workspace_bytes": (_u64, [_u32, _u64]),
+        "dsr_batch_count": (_i32, [_vp, _u32, _u64, _u64, _u64, P(_u64)]),
+        "dsr_launch_batch": (_i32, [_vp, _vp, _u32, _u32, _u64, _vp, _u64, _vp, _u64, _vp, _u64,
+                                    _vp, _u64, P(dsr_batch_tuning), _vp, ctypes.c_int]),
+        "dsr_batch_errors": (_i32, [_vp, _vp, P(_u32), P(_u64), _vp]),
+        "dsr_autotune": (_i32, [_vp, _vp, _u32, _u32, _u64, _vp, _u64, _vp, _u64, _vp, _u64, _vp,
+                                _u64, _vp, P(dsr_batch_tuning), P(ctypes.c_float)]),
+        "dsr_launch_regions": (_i32, [_vp, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u64, _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -114,7 +127,9 @@ def build(force: bool = False) -> str:
 def exported_symbols():
     return ["dsr_create", "dsr_destroy", "dsr_last_error_string", "dsr_stack_init",
             "dsr_validate_region", "dsr_region_extent", "dsr_footprint_model",
-            "dsr_launch_region", "dsr_run_region_host"]
+            "dsr_launch_region", "dsr_run_region_host", "dsr_batch_workspace_bytes",
+            "dsr_batch_count", "dsr_launch_batch", "dsr_batch_errors", "dsr_autotune",
+            "dsr_launch_regions"]
 
 
 # ---------------------------------------------------------------------------
@@ -240,6 +255,66 @@ def dsr_run_region_host(ctx: int, region, images_host, image_bytes: int, out_hos
                                      _ptr(out_host), out_bytes, _ptr(status_host),
                                      _ptr(images_dev), _ptr(out_dev), _ptr(status_dev),
                                      _stream(stream)), ctx)
+
+
+def _tuning(t):
+    if t is None:
+        return None
+    if isinstance(t, dsr_batch_tuning):
+        return ctypes.byref(t)
+    d = dict(t)
+    return ctypes.byref(dsr_batch_tuning(d.get("threads", 256), d.get("slab_bytes", 16384),
+                                         d.get("ctas_per_sm", 0), 0))
+
+
+def dsr_batch_workspace_bytes(n: int, total_teams: int) -> int:
+    return int(lib().dsr_batch_workspace_bytes(n, total_teams))
+
+
+def dsr_batch_count(descs: np.ndarray, image_bytes: int, out_bytes: int, n_status: int) -> int:
+    """descs: DESC_DTYPE host array. Returns the total team count."""
+    t = _u64()
+    _check(lib().dsr_batch_count(descs.ctypes.data, len(descs), image_bytes, out_bytes,
+                                 n_status, ctypes.byref(t)))
+    return t.value
+
+
+def dsr_launch_batch(ctx: int, descs_dev, n: int, program: int, total_teams: int, images, out,
+                     status, workspace, tuning=None, stream=None, use_graph: bool = False):
+    """descs_dev / images / out / status / workspace: device tensors."""
+    _check(lib().dsr_launch_batch(ctx, _ptr(descs_dev), n, program, total_teams, _ptr(images),
+                                  _nbytes(images) if images is not None else 0, _ptr(out),
+                                  _nbytes(out), _ptr(status), _nbytes(status) // 32,
+                                  _ptr(workspace), _nbytes(workspace), _tuning(tuning),
+                                  _stream(stream), 1 if use_graph else 0), ctx)
+
+
+def dsr_batch_errors(ctx: int, workspace, stream=None):
+    e, t = _u32(), _u64()
+    _check(lib().dsr_batch_errors(ctx, _ptr(workspace), ctypes.byref(e), ctypes.byref(t),
+                                  _stream(stream)), ctx)
+    return e.value, t.value
+
+
+def dsr_autotune(ctx: int, descs_dev, n: int, program: int, total_teams: int, images, out,
+                 status, workspace, stream=None):
+    best = dsr_batch_tuning()
+    ms = ctypes.c_float()
+    _check(lib().dsr_autotune(ctx, _ptr(descs_dev), n, program, total_teams, _ptr(images),
+                              _nbytes(images) if images is not None else 0, _ptr(out),
+                              _nbytes(out), _ptr(status), _nbytes(status) // 32,
+                              _ptr(workspace), _nbytes(workspace), _stream(stream),
+                              ctypes.byref(best), ctypes.byref(ms)), ctx)
+    return dict(threads=best.threads, slab_bytes=best.slab_bytes,
+                ctas_per_sm=best.ctas_per_sm), ms.value
+
+
+def dsr_launch_regions(ctx: int, descs: np.ndarray, images, out, status, stream=None):
+    """descs: DESC_DTYPE host array; one plain launch per region."""
+    _check(lib().dsr_launch_regions(ctx, descs.ctypes.data, len(descs), _ptr(images),
+                                    _nbytes(images) if images is not None else 0, _ptr(out),
+                                    _nbytes(out), _ptr(status), _nbytes(status) // 32,
+                                    _stream(stream)), ctx)
 
 
 from .runtime import Runtime  # noqa: E402  (convenience wrapper over the calls above)

@@ -9,6 +9,7 @@
 #include <string>
 
 #include "dsr.h"
+#include "dsr_check.cuh"
 #include "dsr_ctx.h"
 #include "dsr_programs.cuh"
 
@@ -35,12 +36,13 @@ __global__ void __launch_bounds__(MAXT, MINB)
     worker_loop<P>(e);
     return;
   }
-  team_setup(slab_bytes,
+  Stack s;
+  team_setup(s, slab_bytes,
              ovf_per_team ? pool + static_cast<uint64_t>(blockIdx.x) * ovf_per_team : nullptr,
              ovf_per_team, timeout_ns, true);
-  P::master(e);
+  P::master(e, s);
   terminate_workers();
-  team_report(e, st);
+  team_report(e, s, st);
 }
 
 namespace {
@@ -48,12 +50,16 @@ namespace {
 using KernelFn = void (*)(dsr_region_desc, const uint8_t *, uint8_t *, dsr_team_status *,
                           uint8_t *, uint64_t, uint32_t, uint64_t);
 
+// Programs whose launches fill the GPU with many teams (P::kDense) are
+// held to 32 registers, so 2048 threads per SM can be resident; the others
+// get up to 64.
 template <class P>
 KernelFn pick(uint32_t threads) {
-  if (threads <= 128) return plain_kernel<P, 128, 16>;
-  if (threads <= 256) return plain_kernel<P, 256, 8>;
-  if (threads <= 512) return plain_kernel<P, 512, 4>;
-  return plain_kernel<P, 1024, 2>;
+  constexpr int k = P::kDense ? 2 : 1;
+  if (threads <= 128) return plain_kernel<P, 128, 8 * k>;
+  if (threads <= 256) return plain_kernel<P, 256, 4 * k>;
+  if (threads <= 512) return plain_kernel<P, 512, 2 * k>;
+  return plain_kernel<P, 1024, 1 * k>;
 }
 
 KernelFn plain_kernel_for(uint32_t program, uint32_t threads) {
@@ -101,83 +107,33 @@ extern "C" const char *dsr_last_error_string(const dsr_ctx *ctx) {
 }
 
 // ---------------------------------------------------------------------------
-// Descriptor checks (host only)
+// Descriptor checks (host side of dsr_check.cuh)
 // ---------------------------------------------------------------------------
-static uint64_t pad16(uint64_t n) { return (n + 15u) & ~static_cast<uint64_t>(15u); }
-
-static uint32_t desc_width(const dsr_region_desc &d) {
-  const uint32_t w = d.threads > 32u ? d.threads - 32u : 1u;
-  return d.width ? d.width : w;
-}
-
 int32_t dsr_check_shape(const dsr_region_desc *d, const char **why) {
+  static const char *const kWhy[] = {
+      "",
+      "shape out of range (teams >= 1, threads a multiple of 32 in [32, 1024], "
+      "depth 1..4, width <= workers)",
+      "frame sizes must be positive multiples of 4",
+      "image/out offsets must be 16-byte aligned",
+      "frame sizes do not match the program's layout",
+      "unknown program"};
   *why = "";
   if (!d) return (*why = "null descriptor"), DSR_ERR_INVALID;
-  if (d->teams == 0 || d->teams > 0x7fffffffu) return (*why = "teams out of range"), DSR_ERR_INVALID;
-  if (d->threads < 32 || d->threads > DSR_MAX_THREADS || d->threads % 32)
-    return (*why = "threads must be a multiple of 32 in [32, 1024]"), DSR_ERR_INVALID;
-  if (d->depth == 0 || d->depth > DSR_MAX_DEPTH) return (*why = "depth out of range"), DSR_ERR_INVALID;
-  const uint32_t wmax = d->threads > 32u ? d->threads - 32u : 1u;
-  if (d->width > wmax) return (*why = "width exceeds the team's workers"), DSR_ERR_INVALID;
-  for (uint32_t k = 0; k < d->depth; ++k)
-    if (d->frame_bytes[k] == 0 || d->frame_bytes[k] % 4)
-      return (*why = "frame sizes must be positive multiples of 4"), DSR_ERR_INVALID;
-  if (d->image_offset % 16 || d->out_offset % 16)
-    return (*why = "image/out offsets must be 16-byte aligned"), DSR_ERR_INVALID;
-  const uint32_t w = desc_width(*d);
-  switch (d->program) {
-    case DSR_PROG_PAPER_SCALARS:
-      if (d->depth != 1 || d->param == 0 || d->param > 4096 ||
-          d->frame_bytes[0] != ((4u * d->param + 7u) & ~7u) + 8u)
-        return (*why = "paper-scalars frame must hold param ints and a pointer"), DSR_ERR_INVALID;
-      break;
-    case DSR_PROG_PAPER_ARRAYS:
-      if (d->depth != 1 || d->param == 0 || d->param > 4096 ||
-          d->frame_bytes[0] != 4u * d->param * w)
-        return (*why = "paper-arrays frame must hold param int[width] arrays"), DSR_ERR_INVALID;
-      break;
-    case DSR_PROG_SCALARS:
-      if (d->depth != 1 || d->frame_bytes[0] != 16 || d->param == 0)
-        return (*why = "scalars needs depth 1, a 16-byte frame, param >= 1"), DSR_ERR_INVALID;
-      break;
-    case DSR_PROG_NESTED:
-      for (uint32_t k = 0; k < d->depth; ++k)
-        if (d->frame_bytes[k] != 1088)
-          return (*why = "nested frames are 1088 bytes"), DSR_ERR_INVALID;
-      if (d->param == 0 || static_cast<uint64_t>(d->teams) * d->param > 0xffffffffull)
-        return (*why = "nested needs 1 <= teams*param < 2^32"), DSR_ERR_INVALID;
-      break;
-    case DSR_PROG_SWEEP:
-      if (d->depth != 1) return (*why = "sweep has one frame"), DSR_ERR_INVALID;
-      break;
-    case DSR_PROG_HETERO:
-      break;
-    default:
-      return (*why = "unknown program"), DSR_ERR_INVALID;
-  }
-  return DSR_OK;
+  const int e = dsr::shape_error(*d);
+  *why = kWhy[e];
+  return e ? DSR_ERR_INVALID : DSR_OK;
 }
 
 extern "C" int32_t dsr_region_extent(const dsr_region_desc *d, uint64_t *image_bytes,
                                      uint64_t *out_bytes, uint64_t *n_status) {
   const char *why;
   if (dsr_check_shape(d, &why) != DSR_OK) return dsr_fail(nullptr, DSR_ERR_INVALID, "%s", why);
-  const uint64_t T = d->teams, w = desc_width(*d);
-  uint64_t ib = 0, ob = 0;
-  switch (d->program) {
-    case DSR_PROG_PAPER_SCALARS:
-    case DSR_PROG_PAPER_ARRAYS: ob = 4 * T * w; break;
-    case DSR_PROG_SCALARS: ib = 16ull * d->param; ob = 4ull * d->param * T * w; break;
-    case DSR_PROG_NESTED: ib = T * d->depth * 1088ull; ob = 4 * T * d->param; break;
-    case DSR_PROG_SWEEP: ib = T * d->frame_bytes[0]; ob = 4 * T * w; break;
-    case DSR_PROG_HETERO:
-      for (uint32_t k = 0; k < d->depth; ++k) ib += pad16(d->frame_bytes[k]);
-      ob = 4 * T * w;
-      break;
-  }
+  uint64_t ib, ob, ns;
+  dsr::extent(*d, &ib, &ob, &ns);
   if (image_bytes) *image_bytes = ib;
   if (out_bytes) *out_bytes = ob;
-  if (n_status) *n_status = T;
+  if (n_status) *n_status = ns;
   return DSR_OK;
 }
 
@@ -186,15 +142,14 @@ extern "C" int32_t dsr_validate_region(const dsr_region_desc *d, uint64_t image_
   uint64_t ib, ob, ns;
   int32_t rc = dsr_region_extent(d, &ib, &ob, &ns);
   if (rc != DSR_OK) return rc;
-  if (ib && d->image_offset + ib > image_bytes)
-    return dsr_fail(nullptr, DSR_ERR_INVALID, "images end at %llu > %llu bytes",
-                    (unsigned long long)(d->image_offset + ib), (unsigned long long)image_bytes);
-  if (d->out_offset + ob > out_bytes)
-    return dsr_fail(nullptr, DSR_ERR_INVALID, "outputs end at %llu > %llu bytes",
-                    (unsigned long long)(d->out_offset + ob), (unsigned long long)out_bytes);
-  if (static_cast<uint64_t>(d->status_index) + ns > n_status)
-    return dsr_fail(nullptr, DSR_ERR_INVALID, "statuses end at %llu > %llu entries",
-                    (unsigned long long)(d->status_index + ns), (unsigned long long)n_status);
+  if (!dsr::fits(*d, image_bytes, out_bytes, n_status))
+    return dsr_fail(nullptr, DSR_ERR_INVALID,
+                    "region needs images [%llu, +%llu) of %llu, outputs [%llu, +%llu) of %llu, "
+                    "statuses [%u, +%llu) of %llu",
+                    (unsigned long long)d->image_offset, (unsigned long long)ib,
+                    (unsigned long long)image_bytes, (unsigned long long)d->out_offset,
+                    (unsigned long long)ob, (unsigned long long)out_bytes, d->status_index,
+                    (unsigned long long)ns, (unsigned long long)n_status);
   return DSR_OK;
 }
 
@@ -224,7 +179,7 @@ extern "C" int32_t dsr_footprint_model(const dsr_region_desc *d, uint32_t slab_b
   // push order, first fit into the slab, else the overflow slab
   uint64_t sp = 0, spill = 0;
   for (uint32_t k = 0; k < d->depth; ++k) {
-    const uint64_t fp = pad16(d->frame_bytes[k]);
+    const uint64_t fp = dsr::pad16(d->frame_bytes[k]);
     if (sp + fp <= slab_bytes)
       sp += fp;
     else
@@ -336,8 +291,10 @@ extern "C" int32_t dsr_stack_init(dsr_ctx *ctx, uint32_t smem_slab_bytes,
 // ---------------------------------------------------------------------------
 int32_t dsr_launch_plain(dsr_ctx *ctx, const dsr_region_desc *d, const void *images_dev,
                          void *out_dev, dsr_team_status *status_dev, cudaStream_t s) {
-  KernelFn k = plain_kernel_for(d->program, d->threads);
-  k<<<d->teams, d->threads, kCtrlBytes + ctx->slab_bytes, s>>>(
+  // a team without workers gets one worker warp (its region width is 1)
+  const uint32_t block = d->threads > 32u ? d->threads : 64u;
+  KernelFn k = plain_kernel_for(d->program, block);
+  k<<<d->teams, block, kCtrlBytes + ctx->slab_bytes, s>>>(
       *d, static_cast<const uint8_t *>(images_dev), static_cast<uint8_t *>(out_dev), status_dev,
       ctx->pool, ctx->ovf_per_team, ctx->slab_bytes, ctx->timeout_ns);
   cudaError_t e = cudaGetLastError();

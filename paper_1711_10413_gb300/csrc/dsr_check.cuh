@@ -1,0 +1,94 @@
+// dsr_check.cuh -- descriptor checks shared by the host entry points and
+// the kernels that read descriptors from device memory (batched and served
+// launches check every descriptor before running it, so a malformed one
+// turns into DSR_ERR_INVALID in its teams' statuses instead of a fault).
+#pragma once
+
+#include <cstdint>
+
+#include "dsr.h"
+
+#ifdef __CUDACC__
+#define DSR_HD __host__ __device__ __forceinline__
+#else
+#define DSR_HD inline
+#endif
+
+namespace dsr {
+
+DSR_HD uint64_t pad16(uint64_t n) { return (n + 15u) & ~static_cast<uint64_t>(15u); }
+
+DSR_HD uint32_t desc_width(const dsr_region_desc &d) {
+  const uint32_t w = d.threads > 32u ? d.threads - 32u : 1u;
+  return d.width ? d.width : w;
+}
+
+// 0 when the descriptor is well formed; otherwise a short reason code
+// (1 shape, 2 frame sizes, 3 alignment, 4 program layout, 5 unknown program).
+DSR_HD int shape_error(const dsr_region_desc &d) {
+  if (d.teams == 0 || d.teams > 0x7fffffffu) return 1;
+  if (d.threads < 32 || d.threads > DSR_MAX_THREADS || d.threads % 32) return 1;
+  if (d.depth == 0 || d.depth > DSR_MAX_DEPTH) return 1;
+  const uint32_t wmax = d.threads > 32u ? d.threads - 32u : 1u;
+  if (d.width > wmax) return 1;
+  for (uint32_t k = 0; k < d.depth; ++k)
+    if (d.frame_bytes[k] == 0 || d.frame_bytes[k] % 4 || d.frame_bytes[k] > 0x40000000u) return 2;
+  if (d.image_offset % 16 || d.out_offset % 16) return 3;
+  const uint32_t w = desc_width(d);
+  switch (d.program) {
+    case DSR_PROG_PAPER_SCALARS:
+      if (d.depth != 1 || d.param == 0 || d.param > 4096 ||
+          d.frame_bytes[0] != ((4u * d.param + 7u) & ~7u) + 8u)
+        return 4;
+      return 0;
+    case DSR_PROG_PAPER_ARRAYS:
+      if (d.depth != 1 || d.param == 0 || d.param > 4096 || d.frame_bytes[0] != 4u * d.param * w)
+        return 4;
+      return 0;
+    case DSR_PROG_SCALARS:
+      return (d.depth != 1 || d.frame_bytes[0] != 16 || d.param == 0) ? 4 : 0;
+    case DSR_PROG_NESTED:
+      for (uint32_t k = 0; k < d.depth; ++k)
+        if (d.frame_bytes[k] != 1088) return 4;
+      return (d.param == 0 || static_cast<uint64_t>(d.teams) * d.param > 0xffffffffull) ? 4 : 0;
+    case DSR_PROG_SWEEP:
+      return d.depth != 1 ? 4 : 0;
+    case DSR_PROG_HETERO:
+      return 0;
+    default:
+      return 5;
+  }
+}
+
+// Input-image bytes, output bytes and status entries of a well-formed
+// descriptor.
+DSR_HD void extent(const dsr_region_desc &d, uint64_t *ib, uint64_t *ob, uint64_t *ns) {
+  const uint64_t T = d.teams, w = desc_width(d);
+  uint64_t i = 0, o = 0;
+  switch (d.program) {
+    case DSR_PROG_PAPER_SCALARS:
+    case DSR_PROG_PAPER_ARRAYS: o = 4 * T * w; break;
+    case DSR_PROG_SCALARS: i = 16ull * d.param; o = 4ull * d.param * T * w; break;
+    case DSR_PROG_NESTED: i = T * d.depth * 1088ull; o = 4 * T * d.param; break;
+    case DSR_PROG_SWEEP: i = T * d.frame_bytes[0]; o = 4 * T * w; break;
+    case DSR_PROG_HETERO:
+      for (uint32_t k = 0; k < d.depth; ++k) i += pad16(d.frame_bytes[k]);
+      o = 4 * T * w;
+      break;
+  }
+  *ib = i;
+  *ob = o;
+  *ns = T;
+}
+
+// The descriptor fits the buffers it indexes.
+DSR_HD bool fits(const dsr_region_desc &d, uint64_t image_bytes, uint64_t out_bytes,
+                 uint64_t n_status) {
+  uint64_t ib, ob, ns;
+  extent(d, &ib, &ob, &ns);
+  if (ib && (d.image_offset > image_bytes || ib > image_bytes - d.image_offset)) return false;
+  if (d.out_offset > out_bytes || ob > out_bytes - d.out_offset) return false;
+  return static_cast<uint64_t>(d.status_index) + ns <= n_status;
+}
+
+}  // namespace dsr

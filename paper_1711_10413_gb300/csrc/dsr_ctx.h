@@ -40,4 +40,5 @@ int32_t dsr_launch_plain(dsr_ctx *ctx, const dsr_region_desc *d, const void *ima
                          void *out_dev, dsr_team_status *status_dev, cudaStream_t s);
 // Hooks of the batched / served forms into the context's lifecycle.
 void dsr_ctx_release(dsr_ctx *ctx);
+void dsr_serve_release(dsr_ctx *ctx);
 int32_t dsr_ctx_stack_changed(dsr_ctx *ctx, uint32_t smem_per_team);

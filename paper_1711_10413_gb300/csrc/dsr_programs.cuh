@@ -19,12 +19,14 @@ __device__ __forceinline__ const uint32_t *frame_words(uint32_t k) {
 // adds the sum of the c_i to a[team*W' + tid].
 // ---------------------------------------------------------------------------
 struct ProgPaperScalars {
+  static constexpr uint32_t kProgram = DSR_PROG_PAPER_SCALARS;
+  static constexpr bool kDense = false;
   __device__ static uint32_t ptr_off(uint32_t n) { return (4u * n + 7u) & ~7u; }
 
-  __device__ static void master(const Env &e) {
+  __device__ static void master(const Env &e, Stack &s) {
     const dsr_region_desc &d = *e.d;
     const uint32_t n = d.param;
-    uint8_t *f = push(d.frame_bytes[0]);
+    uint8_t *f = push(s, d.frame_bytes[0]);
     if (!f) return;
     if (lane_id() == 0) {
       uint32_t *c = reinterpret_cast<uint32_t *>(f);
@@ -35,7 +37,7 @@ struct ProgPaperScalars {
     }
     __syncwarp();
     parallel<ProgPaperScalars>(e, 0, region_width(d), 0);
-    pop(f);
+    pop(s, f, d.frame_bytes[0]);
   }
 
   __device__ static void body(const Env &e, uint32_t, uint32_t tid, uint32_t n, uint32_t) {
@@ -55,15 +57,17 @@ struct ProgPaperScalars {
 // sum_m d_m[tid] to a[team*W' + tid].
 // ---------------------------------------------------------------------------
 struct ProgPaperArrays {
-  __device__ static void master(const Env &e) {
+  static constexpr uint32_t kProgram = DSR_PROG_PAPER_ARRAYS;
+  static constexpr bool kDense = false;
+  __device__ static void master(const Env &e, Stack &s) {
     const dsr_region_desc &d = *e.d;
-    uint8_t *f = push(d.frame_bytes[0]);
+    uint8_t *f = push(s, d.frame_bytes[0]);
     if (!f) return;
     uint32_t *w = reinterpret_cast<uint32_t *>(f);
     for (uint32_t i = lane_id(); i < d.frame_bytes[0] / 4u; i += 32u) w[i] = 10u;
     __syncwarp();
     parallel<ProgPaperArrays>(e, 0, region_width(d), 0);
-    pop(f);
+    pop(s, f, d.frame_bytes[0]);
   }
 
   __device__ static void body(const Env &e, uint32_t, uint32_t tid, uint32_t n, uint32_t) {
@@ -78,25 +82,38 @@ struct ProgPaperArrays {
 // ---------------------------------------------------------------------------
 // Config 1: R = param sequential regions per team, each pushing int32 s[4]
 // from image[r]; out[(r*T + team)*W' + tid] = (s0*tid + s1) ^
-// ((s2 >> (tid & 7)) + s3). The master loads region r+1's image before it
-// forks region r, so the load overlaps the parallel region.
+// ((s2 >> (tid & 7)) + s3). The master warp loads the frames of the next
+// 32 regions while the current ones run (one region per lane).
 // ---------------------------------------------------------------------------
 struct ProgScalars {
-  __device__ static void master(const Env &e) {
+  static constexpr uint32_t kProgram = DSR_PROG_SCALARS;
+  static constexpr bool kDense = false;
+  __device__ static void master(const Env &e, Stack &s) {
     const dsr_region_desc &d = *e.d;
-    const uint32_t R = d.param, width = region_width(d);
+    const uint32_t R = d.param, width = region_width(d), lane = lane_id();
     const uint4 *img = reinterpret_cast<const uint4 *>(e.images + d.image_offset);
-    uint4 next = lane_id() == 0 ? __ldg(img) : make_uint4(0, 0, 0, 0);
+    // lane l holds the frame of region (32 * batch + l): the loads for the
+    // next batch are in flight while the current 32 regions run
+    const uint4 zero = make_uint4(0, 0, 0, 0);
+    uint4 cur = lane < R ? __ldg(img + lane) : zero;
+    uint4 nxt = 32u + lane < R ? __ldg(img + 32u + lane) : zero;
     for (uint32_t r = 0; r < R; ++r) {
-      uint8_t *f = push(16);
-      if (!f) return;
-      if (lane_id() == 0) {
-        *reinterpret_cast<uint4 *>(f) = next;
-        if (r + 1 < R) next = __ldg(img + r + 1);
+      const uint32_t l = r & 31u;
+      if (l == 0 && r != 0) {
+        cur = nxt;
+        nxt = r + 32u + lane < R ? __ldg(img + r + 32u + lane) : zero;
       }
+      uint4 v;
+      v.x = __shfl_sync(0xffffffffu, cur.x, l);
+      v.y = __shfl_sync(0xffffffffu, cur.y, l);
+      v.z = __shfl_sync(0xffffffffu, cur.z, l);
+      v.w = __shfl_sync(0xffffffffu, cur.w, l);
+      uint8_t *f = push(s, 16);
+      if (!f) return;
+      if (lane == 0) *reinterpret_cast<uint4 *>(f) = v;
       __syncwarp();
       parallel<ProgScalars>(e, 0, width, r);
-      pop(f);
+      pop(s, f, 16);
     }
   }
 
@@ -115,22 +132,34 @@ struct ProgScalars {
 //   k < D: F_k.arr[i] = mix32(F_k.arr[i] + i) for the worker's strided i;
 //          after the join the master stores sum(F_k.arr) in F_k.s[15];
 //   k = D: out[e] = mix32(e ^ sum_m (F_m.arr[j & 255] ^ F_m.s[j & 15])),
-//          e = team*E + j, for the worker's strided j < E (E = param).
+//          e = team*E + j, for every j < E (E = param), each j by one
+//          worker.
 // On the way out chk[k-1] = F_k.s[15], then F_k is popped.
 // ---------------------------------------------------------------------------
 struct ProgNested {
+  static constexpr uint32_t kProgram = DSR_PROG_NESTED;
+  static constexpr bool kDense = true;
   enum : uint32_t { kUpdate = 0, kInner = 1 };
 
-  __device__ static void master(const Env &e) {
+  __device__ static void master(const Env &e, Stack &s) {
     const dsr_region_desc &d = *e.d;
     const uint32_t D = d.depth, width = region_width(d);
     const uint8_t *timg = e.images + d.image_offset + static_cast<uint64_t>(e.team) * D * 1088u;
+    // all levels' images at once, into the slab slots the pushes will take
+    const uint8_t *expect = slab_base() + s.sp;
+    const bool staged = stage(s, timg, D * 1088u);
+    if (!staged && lane_id() == 0) prefetch_l2(timg, D * 1088u);
     for (uint32_t k = 1; k <= D; ++k) {
       bool sm;
-      uint8_t *f = push(d.frame_bytes[k - 1], &sm);
+      uint8_t *f = push(s, d.frame_bytes[k - 1], &sm);
       if (!f) return;
-      fill(f, sm, timg + (k - 1) * 1088u, 1088u, mix32(e.team * 8u + k));
-      if (!team_ok()) return;
+      const uint32_t key = mix32(e.team * 8u + k);
+      if (staged && k == 1) wait_staged(s);
+      if (staged && f == expect + (k - 1) * 1088u)
+        key_in_place(f, 1088u, key);
+      else
+        fill<!kDense>(s, f, sm, timg + (k - 1) * 1088u, 1088u, key);
+      if (s.status() != DSR_OK) return;
       if (k > 1 && lane_id() == 0) reinterpret_cast<uint32_t *>(f)[0] ^= frame_words(k - 2)[15];
       __syncwarp();
       parallel<ProgNested>(e, k < D ? kUpdate : kInner, width, k);
@@ -143,7 +172,7 @@ struct ProgNested {
     for (uint32_t k = D; k >= 1; --k) {
       const uint8_t *f = ctrl()->frames[k - 1].ptr;
       if (lane_id() == 0) ctrl()->chk[k - 1] = reinterpret_cast<const uint32_t *>(f)[15];
-      pop(f);
+      pop(s, f, d.frame_bytes[k - 1]);
     }
   }
 
@@ -155,17 +184,52 @@ struct ProgNested {
       return;
     }
     const uint32_t D = e.d->depth, E = e.d->param;
-    const uint32_t *f[DSR_MAX_DEPTH];
-#pragma unroll
-    for (uint32_t m = 0; m < DSR_MAX_DEPTH; ++m) f[m] = m < D ? frame_words(m) : nullptr;
     uint32_t *o = reinterpret_cast<uint32_t *>(e.out + e.d->out_offset) +
                   static_cast<uint64_t>(e.team) * E;
     const uint32_t ebase = e.team * E;
-    for (uint32_t j = tid; j < E; j += n) {
-      uint32_t acc = 0;
+    bool all_smem = true;
+    for (uint32_t m = 0; m < D; ++m) all_smem &= ctrl()->frames[m].in_smem != 0;
+    // Each element j is written by exactly one worker; the workers take
+    // groups of 4 consecutive elements (16-byte frame reads and output
+    // stores) when E is a multiple of 4. arr[j & 255] and s[j & 15] of a
+    // group are 4 consecutive words (256 and 16 are multiples of 4).
+    if ((E & 3u) == 0 && all_smem) {
+      // frames addressed as byte offsets into the team's shared memory
+      uint32_t fo[DSR_MAX_DEPTH];
 #pragma unroll
       for (uint32_t m = 0; m < DSR_MAX_DEPTH; ++m)
-        if (m < D) acc += f[m][16u + (j & 255u)] ^ f[m][j & 15u];
+        fo[m] = m < D ? static_cast<uint32_t>(ctrl()->frames[m].ptr - dsr_smem) : 0u;
+      for (uint32_t g = tid; g < (E >> 2); g += n) {
+        const uint32_t j0 = g << 2;
+        uint4 acc = make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (uint32_t m = 0; m < DSR_MAX_DEPTH; ++m) {
+          if (m < D) {
+            const uint4 a = *reinterpret_cast<const uint4 *>(dsr_smem + fo[m] + 64u +
+                                                             4u * (j0 & 255u));
+            const uint4 sv = *reinterpret_cast<const uint4 *>(dsr_smem + fo[m] + 4u * (j0 & 15u));
+            acc.x += a.x ^ sv.x;
+            acc.y += a.y ^ sv.y;
+            acc.z += a.z ^ sv.z;
+            acc.w += a.w ^ sv.w;
+          }
+        }
+        const uint32_t e0 = ebase + j0;
+        uint4 r;
+        r.x = mix32(e0 ^ acc.x);
+        r.y = mix32((e0 + 1u) ^ acc.y);
+        r.z = mix32((e0 + 2u) ^ acc.z);
+        r.w = mix32((e0 + 3u) ^ acc.w);
+        *reinterpret_cast<uint4 *>(o + j0) = r;
+      }
+      return;
+    }
+    for (uint32_t j = tid; j < E; j += n) {
+      uint32_t acc = 0;
+      for (uint32_t m = 0; m < D; ++m) {
+        const uint32_t *f = frame_words(m);
+        acc += f[16u + (j & 255u)] ^ f[j & 15u];
+      }
       o[j] = mix32((ebase + j) ^ acc);
     }
   }
@@ -177,16 +241,18 @@ struct ProgNested {
 // order, each addition rounded to fp32 (no contraction).
 // ---------------------------------------------------------------------------
 struct ProgSweep {
-  __device__ static void master(const Env &e) {
+  static constexpr uint32_t kProgram = DSR_PROG_SWEEP;
+  static constexpr bool kDense = false;
+  __device__ static void master(const Env &e, Stack &s) {
     const dsr_region_desc &d = *e.d;
     const uint32_t S = d.frame_bytes[0];
     bool sm;
-    uint8_t *f = push(S, &sm);
+    uint8_t *f = push(s, S, &sm);
     if (!f) return;
-    fill(f, sm, e.images + d.image_offset + static_cast<uint64_t>(e.team) * S, S, 0u);
-    if (!team_ok()) return;
+    fill<!kDense>(s, f, sm, e.images + d.image_offset + static_cast<uint64_t>(e.team) * S, S, 0u);
+    if (s.status() != DSR_OK) return;
     parallel<ProgSweep>(e, 0, region_width(d), 0);
-    pop(f);
+    pop(s, f, S);
   }
 
   __device__ static void body(const Env &e, uint32_t, uint32_t tid, uint32_t n, uint32_t) {
@@ -208,20 +274,35 @@ struct ProgSweep {
 // chk[D-1] = F_D[0]; the frames are popped in reverse order.
 // ---------------------------------------------------------------------------
 struct ProgHetero {
+  static constexpr uint32_t kProgram = DSR_PROG_HETERO;
+  static constexpr bool kDense = false;
   enum : uint32_t { kUpdate = 0, kInner = 1 };
 
-  __device__ static void master(const Env &e) {
+  __device__ static void master(const Env &e, Stack &s) {
     const dsr_region_desc &d = *e.d;
     const uint32_t D = d.depth, width = region_width(d);
     const uint8_t *img = e.images + d.image_offset;
+    uint32_t total = 0;
+    for (uint32_t k = 0; k < D; ++k) total += (d.frame_bytes[k] + 15u) & ~15u;
+    // every level's image at once, into the slab slots the pushes will take
+    // (the images are laid out per level, 16-byte padded, as the slab is)
+    uint8_t *expect = slab_base() + s.sp;
+    const bool staged = stage(s, img, total);
+    if (!staged && lane_id() == 0) prefetch_l2(img, total);
     uint32_t c_prev = 0;
     for (uint32_t k = 1; k <= D; ++k) {
       const uint32_t S = d.frame_bytes[k - 1];
       bool sm;
-      uint8_t *f = push(S, &sm);
+      uint8_t *f = push(s, S, &sm);
       if (!f) return;
-      fill(f, sm, img, S, mix32(d.salt + e.team * 8u + k));
-      if (!team_ok()) return;
+      const uint32_t key = mix32(d.salt + e.team * 8u + k);
+      if (staged && k == 1) wait_staged(s);
+      if (staged && f == expect)
+        key_in_place(f, S, key);
+      else
+        fill<!kDense>(s, f, sm, img, S, key);
+      expect += (S + 15u) & ~15u;
+      if (s.status() != DSR_OK) return;
       img += (S + 15u) & ~15u;
       if (k > 1 && lane_id() == 0) reinterpret_cast<uint32_t *>(f)[0] ^= c_prev;
       __syncwarp();
@@ -232,7 +313,7 @@ struct ProgHetero {
       }
     }
     if (lane_id() == 0) ctrl()->chk[D - 1] = frame_words(D - 1)[0];
-    for (uint32_t k = D; k >= 1; --k) pop(ctrl()->frames[k - 1].ptr);
+    for (uint32_t k = D; k >= 1; --k) pop(s, ctrl()->frames[k - 1].ptr, d.frame_bytes[k - 1]);
   }
 
   __device__ static void body(const Env &e, uint32_t work, uint32_t tid, uint32_t n,

@@ -13,16 +13,17 @@
 // arrives at the fork barrier, and waits at the join barrier until the
 // workers finish the body. Named barriers (Sec. 4: "named barriers are used
 // to control the execution of master and worker threads") keep fork and
-// join apart: bar.sync kForkBar / kJoinBar with the team's thread count.
-// Workers beyond the region's thread count skip the body but still reach
-// the join (the exec_status test of Fig. "codegen-worker").
+// join apart, each used as a producer/consumer pair with the team's thread
+// count: at the fork the master arrives (bar.arrive, it need not wait) and
+// the workers wait (bar.sync); at the join the workers arrive and the
+// master waits. Workers beyond the region's thread count skip the body but
+// still reach the join (the exec_status test of Fig. "codegen-worker").
 //
 // Shared locals (Sec. 5.1-5.3): the master pushes a frame per call level on
-// a LIFO stack. The stack pointers (slab and overflow; the paper's shared
-// stack pointer register of Sec. 5.3, %SPSH / VRShared) live in the team's
-// control block in shared memory, where every master-warp lane reads them
-// and lane 0 updates them, which keeps the kernels within 32 registers.
-// A frame goes to the team's shared-memory slab when it fits, otherwise to
+// a LIFO stack. The stack pointers (slab and overflow) live in registers of
+// the master warp, identical in all 32 lanes, as the paper's shared stack
+// pointer register does (Sec. 5.3, %SPSH / VRShared); lane 0 records each
+// frame in the control block's frame table. A frame goes to the team's shared-memory slab when it fits, otherwise to
 // the team's global overflow slab (the global-memory safety net of Sec. 5.2
 // and the runtime-managed global stack of Sec. 7); a frame never straddles
 // the two. The frame table in the control block is the list of references
@@ -39,7 +40,9 @@ namespace dsr {
 constexpr uint32_t kForkBar = 1;
 constexpr uint32_t kJoinBar = 2;
 constexpr uint32_t kTerminate = 0xFFFFFFFFu;
-constexpr uint32_t kCtrlBytes = 256;  // control block, slab starts after it
+constexpr uint32_t kCopyWork = 0xFFFFFFF0u;  // runtime-internal: workers copy a frame image
+constexpr uint32_t kCtrlBytes = 384;  // control block, slab starts after it
+constexpr uint32_t kParallelCopyBytes = 2048;  // frames filled by the workers from this size
 
 struct FrameEnt {
   uint8_t *ptr;      // generic address of the frame (shared or global)
@@ -48,27 +51,25 @@ struct FrameEnt {
 };
 
 struct __align__(16) Ctrl {
-  // handoff: written by the master before the fork barrier, read by workers
+  // handoff: written by the master before the fork, read by the workers
   uint32_t work;      // body id of the current parallel region or kTerminate
   uint32_t nthreads;  // threads of the current parallel region
   uint32_t arg;       // per-region argument (level, region index)
   uint32_t task;      // batched launch: current task
-  // the team's stack (master warp only; every lane reads, lane 0 writes)
-  uint32_t sp;        // slab bytes reserved
-  uint32_t depth;     // live frames
-  uint32_t hwm;       // peak reserved bytes, slab + overflow
-  uint32_t spill;     // peak reserved overflow bytes
-  uint64_t gsp;       // overflow-slab bytes reserved
-  int32_t status;
-  uint32_t phase;     // parity of the fill mbarrier
   uint64_t mbar;      // mbarrier completing bulk-copy fills
-  uint32_t slab_bytes;
-  uint32_t pad0;
+  uint64_t timeout_ns;
   uint8_t *ovf;       // this team's overflow slab
   uint64_t ovf_bytes;
-  uint64_t timeout_ns;
+  uint32_t slab_bytes;  // capacity of the shared-memory slab
+  uint32_t team;        // batched launch: the current task's team
+  uint32_t pad0[2];
   uint32_t chk[DSR_MAX_DEPTH];
   FrameEnt frames[DSR_MAX_FRAMES];
+  dsr_region_desc desc;  // batched launch: the current task's region
+  const uint8_t *copy_src;  // kCopyWork arguments
+  uint8_t *copy_dst;
+  uint32_t copy_bytes;
+  uint32_t copy_key;
 };
 static_assert(sizeof(Ctrl) <= kCtrlBytes, "control block too large");
 
@@ -77,6 +78,10 @@ static_assert(sizeof(Ctrl) <= kCtrlBytes, "control block too large");
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void named_bar(uint32_t id, uint32_t nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ void named_arrive(uint32_t id, uint32_t nthreads) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 __device__ __forceinline__ uint64_t globaltimer() {
@@ -139,6 +144,17 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
       : "memory");
 }
 
+// Hint: pull [src, src + bytes) into L2 (bulk prefetch; src 16-byte
+// aligned, bytes a multiple of 16). Issued by one thread; no completion.
+__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
+  if (((reinterpret_cast<uintptr_t>(src) | bytes) & 15u) != 0) return;
+  const uint8_t *p = static_cast<const uint8_t *>(src);
+  for (uint32_t off = 0; off < bytes; off += 65536u) {
+    const uint32_t n = bytes - off < 65536u ? bytes - off : 65536u;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p + off), "r"(n) : "memory");
+  }
+}
+
 // 32-bit finaliser of MurmurHash3 (Appleby, public domain).
 __device__ __forceinline__ uint32_t mix32(uint32_t h) {
   h ^= h >> 16;
@@ -173,116 +189,173 @@ struct Env {
   uint32_t team;             // team number (omp_get_team_num)
 };
 
-// Team setup (master warp): the stack starts empty.
-__device__ __forceinline__ void team_setup(uint32_t slab_bytes, uint8_t *ovf, uint64_t ovf_bytes,
-                                           uint64_t timeout_ns, bool first) {
+// The master warp's stack state, in registers, identical in all 32 lanes.
+// Nothing here is read back from memory on the handoff path: a load issued
+// right after the join barrier waits for the workers' outstanding stores,
+// so push and pop work from registers alone (the frame table in the control
+// block is written for the workers, never read by the master's pop).
+struct Stack {
+  uint32_t slab_bytes;  // capacity of the shared-memory slab
+  uint32_t sp;          // slab bytes reserved
+  uint32_t gsp;         // overflow-slab bytes reserved
+  uint32_t hwm;         // peak reserved bytes, slab + overflow
+  uint32_t spill;       // peak reserved overflow bytes
+  uint32_t bits;        // status (bits 0-7) | fill-mbarrier parity (bit 8) |
+                        // staged copy pending (bit 9) | live depth (bits 12-15) |
+                        // frame k in the slab (bit 16 + k)
+
+  __device__ __forceinline__ int32_t status() const { return static_cast<int32_t>(bits & 0xffu); }
+  __device__ __forceinline__ uint32_t phase() const { return (bits >> 8) & 1u; }
+  __device__ __forceinline__ uint32_t depth() const { return (bits >> 12) & 0xfu; }
+};
+
+// Team setup (master warp): the stack starts empty. `first` initialises the
+// fill mbarrier (once per CTA).
+__device__ __forceinline__ void team_setup(Stack &s, uint32_t slab_bytes, uint8_t *ovf,
+                                           uint64_t ovf_bytes, uint64_t timeout_ns, bool first) {
   Ctrl *c = ctrl();
   if (lane_id() == 0) {
-    c->sp = 0;
-    c->depth = 0;
-    c->hwm = 0;
-    c->spill = 0;
-    c->gsp = 0;
-    c->status = DSR_OK;
-    c->slab_bytes = slab_bytes;
     c->ovf = ovf;
     c->ovf_bytes = ovf_bytes;
     c->timeout_ns = timeout_ns;
+    c->slab_bytes = slab_bytes;
 #pragma unroll
     for (int k = 0; k < DSR_MAX_DEPTH; ++k) c->chk[k] = 0;
-    if (first) {
-      c->phase = 0;
-      mbar_init(&c->mbar, 1);
-    }
+    if (first) mbar_init(&c->mbar, 1);
   }
+  s.bits = first ? 0u : (s.bits & 0x100u);  // the mbarrier's parity carries over
+  s.slab_bytes = slab_bytes;
+  s.sp = 0;
+  s.gsp = 0;
+  s.hwm = 0;
+  s.spill = 0;
   __syncwarp();
 }
 
-__device__ __forceinline__ void set_status(int32_t st) {
-  __syncwarp();
-  if (lane_id() == 0 && ctrl()->status == DSR_OK) ctrl()->status = st;
-  __syncwarp();
+__device__ __forceinline__ void set_status(Stack &s, int32_t st) {
+  if (s.status() == DSR_OK) s.bits = (s.bits & ~0xffu) | static_cast<uint32_t>(st);
 }
-
-__device__ __forceinline__ bool team_ok() { return ctrl()->status == DSR_OK; }
 
 // Push `bytes` (whole master warp). Returns the frame's generic address, or
 // nullptr with status OVERFLOW when neither slab has room or the frame table
 // is full.
-__device__ __forceinline__ uint8_t *push(uint32_t bytes, bool *in_smem = nullptr) {
-  Ctrl *c = ctrl();
+__device__ __forceinline__ uint8_t *push(Stack &s, uint32_t bytes, bool *in_smem = nullptr) {
   const uint32_t fp = (bytes + 15u) & ~15u;
-  if (c->status != DSR_OK) return nullptr;
-  const uint32_t sp = c->sp, depth = c->depth;
-  const uint64_t gsp = c->gsp;
+  if (s.status() != DSR_OK) return nullptr;
+  const uint32_t depth = s.depth();
   uint8_t *p = nullptr;
   uint32_t sm = 0;
   if (depth < DSR_MAX_FRAMES) {
-    if (sp + fp <= c->slab_bytes) {
-      p = slab_base() + sp;
+    if (s.sp + fp <= s.slab_bytes) {
+      p = slab_base() + s.sp;
       sm = 1;
-    } else if (gsp + fp <= c->ovf_bytes) {
-      p = c->ovf + gsp;
+    } else {
+      const Ctrl *c = ctrl();  // overflow path: read the team's overflow slab
+      if (static_cast<uint64_t>(s.gsp) + fp <= c->ovf_bytes) p = c->ovf + s.gsp;
     }
   }
   if (!p) {
-    set_status(DSR_ERR_OVERFLOW);
+    set_status(s, DSR_ERR_OVERFLOW);
     return nullptr;
   }
-  __syncwarp();
+  if (sm)
+    s.sp += fp;
+  else
+    s.gsp += fp;
+  s.bits = (s.bits & ~0xf000u) | ((depth + 1u) << 12) | (sm << (16u + depth));
   if (lane_id() == 0) {
-    const uint32_t nsp = sm ? sp + fp : sp;
-    const uint64_t ngsp = sm ? gsp : gsp + fp;
-    c->sp = nsp;
-    c->gsp = ngsp;
-    c->depth = depth + 1;
-    c->frames[depth].ptr = p;
-    c->frames[depth].bytes = bytes;
-    c->frames[depth].in_smem = sm;
-    const uint64_t live = static_cast<uint64_t>(nsp) + ngsp;
-    if (live > c->hwm) c->hwm = static_cast<uint32_t>(live);
-    if (ngsp > c->spill) c->spill = static_cast<uint32_t>(ngsp);
+    Ctrl *c = ctrl();
+    FrameEnt f;
+    f.ptr = p;
+    f.bytes = bytes;
+    f.in_smem = sm;
+    c->frames[depth] = f;
   }
-  __syncwarp();
+  s.hwm = max(s.hwm, s.sp + s.gsp);
+  s.spill = max(s.spill, s.gsp);
   if (in_smem) *in_smem = sm != 0;
   return p;
 }
 
-// Pop `p`, which must be the top frame (else status LIFO, nothing popped).
-__device__ __forceinline__ int32_t pop(const uint8_t *p) {
-  Ctrl *c = ctrl();
-  const uint32_t depth = c->depth;
-  if (depth == 0 || c->frames[depth - 1].ptr != p) {
-    set_status(DSR_ERR_LIFO);
+// Pop the top frame `p` of `bytes` bytes. A frame's address is unique while
+// it is live, so `p` is the top frame exactly when it ends at the stack
+// pointer of the slab the top frame was placed in; anything else is LIFO
+// misuse (status LIFO, nothing popped).
+__device__ __forceinline__ int32_t pop(Stack &s, const uint8_t *p, uint32_t bytes) {
+  const uint32_t fp = (bytes + 15u) & ~15u;
+  const uint32_t depth = s.depth();
+  bool ok = depth != 0;
+  uint32_t sm = 0;
+  if (ok) {
+    sm = (s.bits >> (16u + depth - 1u)) & 1u;
+    if (sm) {
+      ok = fp <= s.sp && p == slab_base() + (s.sp - fp);
+    } else {
+      const Ctrl *c = ctrl();  // overflow path
+      ok = fp <= s.gsp && p == c->ovf + (s.gsp - fp);
+    }
+  }
+  if (!ok) {
+    set_status(s, DSR_ERR_LIFO);
     return DSR_ERR_LIFO;
   }
-  const FrameEnt f = c->frames[depth - 1];
-  const uint32_t fp = (f.bytes + 15u) & ~15u;
-  __syncwarp();
-  if (lane_id() == 0) {
-    if (f.in_smem)
-      c->sp -= fp;
-    else
-      c->gsp -= fp;
-    c->depth = depth - 1;
-  }
-  __syncwarp();
+  if (sm)
+    s.sp -= fp;
+  else
+    s.gsp -= fp;
+  s.bits = (s.bits & ~(0xf000u | (1u << (16u + depth - 1u)))) | ((depth - 1u) << 12);
   return DSR_OK;
+}
+
+// Pop whatever is on top (error unwinding; reads the frame table).
+__device__ __forceinline__ void pop_top(Stack &s) {
+  __syncwarp();
+  const FrameEnt f = ctrl()->frames[s.depth() - 1];
+  const int32_t keep = s.status();
+  s.bits &= ~0xffu;
+  pop(s, f.ptr, f.bytes);
+  s.bits = (s.bits & ~0xffu) | static_cast<uint32_t>(keep);
+}
+
+// dst[w] = src[w] ^ key for the words of `bytes` (a multiple of 4), split
+// over `nthr` threads (this one is `idx`); 16-byte vectors when aligned.
+__device__ __forceinline__ void copy_xor(uint8_t *dst, const uint8_t *src, uint32_t bytes,
+                                         uint32_t key, uint32_t idx, uint32_t nthr) {
+  uint32_t w0 = 0;
+  if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0) {
+    const uint32_t nv = bytes / 16u;
+    const uint4 *sv = reinterpret_cast<const uint4 *>(src);
+    uint4 *dv = reinterpret_cast<uint4 *>(dst);
+    for (uint32_t i = idx; i < nv; i += nthr) {
+      uint4 x = __ldg(sv + i);
+      x.x ^= key;
+      x.y ^= key;
+      x.z ^= key;
+      x.w ^= key;
+      dv[i] = x;
+    }
+    w0 = nv * 4u;
+  }
+  const uint32_t *sw = reinterpret_cast<const uint32_t *>(src);
+  uint32_t *dw = reinterpret_cast<uint32_t *>(dst);
+  for (uint32_t w = w0 + idx; w < bytes / 4u; w += nthr) dw[w] = __ldg(sw + w) ^ key;
 }
 
 // Fill a frame from a global image, word by word XOR `key` (master warp).
 // Shared-memory frames with 16-byte aligned source and size take one bulk
 // copy issued by the master (a single thread moves the whole frame) and are
-// then keyed in place; other frames are copied by the 32 lanes with 16-byte
-// vector accesses where alignment allows.
-__device__ __forceinline__ void fill(uint8_t *dst, bool dst_smem, const uint8_t *src,
+// then keyed in place; other frames are copied by the 32 lanes, with 16-byte
+// vector accesses where alignment allows (kWide) or word by word (the
+// register-lean form used by kernels held to 32 registers).
+template <bool kWide>
+__device__ __forceinline__ void fill(Stack &s, uint8_t *dst, bool dst_smem, const uint8_t *src,
                                      uint32_t bytes, uint32_t key) {
   const uint32_t lane = lane_id();
-  Ctrl *c = ctrl();
   const bool aligned = ((reinterpret_cast<uintptr_t>(src) | bytes) & 15u) == 0;
   if (dst_smem && aligned && bytes >= 64) {
+    Ctrl *c = ctrl();
     uint64_t *bar = &c->mbar;
-    const uint32_t phase = c->phase;
+    const uint32_t phase = s.phase();
     if (lane == 0) {
       fence_proxy_async_smem();
       mbar_expect_tx(bar, bytes);
@@ -297,10 +370,9 @@ __device__ __forceinline__ void fill(uint8_t *dst, bool dst_smem, const uint8_t 
       // the copy is still in flight: wait for it (bounded again) before the
       // slab can be reused or the CTA ends
       mbar_wait(bar, phase, tmo);
-      set_status(DSR_ERR_TIMEOUT);
+      set_status(s, DSR_ERR_TIMEOUT);
     }
-    __syncwarp();
-    if (lane == 0) c->phase = phase ^ 1u;
+    s.bits ^= 0x100u;
     if (key != 0) {
       uint4 *v = reinterpret_cast<uint4 *>(dst);
       for (uint32_t i = lane; i < bytes / 16u; i += 32u) {
@@ -312,7 +384,21 @@ __device__ __forceinline__ void fill(uint8_t *dst, bool dst_smem, const uint8_t 
         v[i] = x;
       }
     }
-  } else if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0) {
+  } else if (bytes >= kParallelCopyBytes) {
+    // a large frame outside the slab: the workers copy it (a runtime-owned
+    // initialisation between two fork/join barriers, no user code runs)
+    if (lane == 0) {
+      Ctrl *c = ctrl();
+      c->work = kCopyWork;
+      c->copy_src = src;
+      c->copy_dst = dst;
+      c->copy_bytes = bytes;
+      c->copy_key = key;
+    }
+    named_arrive(kForkBar, team_threads());
+    named_bar(kJoinBar, team_threads());
+  } else if (kWide &&
+             ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0) {
     const uint32_t nv = bytes / 16u;
     const uint4 *sv = reinterpret_cast<const uint4 *>(src);
     uint4 *dv = reinterpret_cast<uint4 *>(dst);
@@ -344,6 +430,65 @@ __device__ __forceinline__ void fill(uint8_t *dst, bool dst_smem, const uint8_t 
   __syncwarp();
 }
 
+// Eager staging. When the frames a team will push next all fit in the
+// slab, their addresses are known before the pushes (the slab is a bump
+// allocator and frames are pushed in order), so the master can start one
+// bulk copy per frame image at once, into those future slots, and pay the
+// memory latency once instead of once per level. stage() issues the copy
+// (source 16-byte aligned, size a multiple of 16) and returns whether it
+// did. The images must lie in memory as the frames will in the slab: in
+// push order, each padded to 16 bytes, so one contiguous copy stages them
+// all. wait_staged() waits for the copy (once, before the first staged
+// frame is used); key_in_place() then completes each frame's fill.
+__device__ __forceinline__ bool stage(Stack &s, const uint8_t *src, uint32_t total) {
+  if (((reinterpret_cast<uintptr_t>(src) | total) & 15u) || total == 0 ||
+      s.sp + total > s.slab_bytes || s.status() != DSR_OK)
+    return false;
+  if (lane_id() == 0) {
+    Ctrl *c = ctrl();
+    fence_proxy_async_smem();
+    mbar_expect_tx(&c->mbar, total);
+    for (uint32_t off = 0; off < total; off += 32768u) {
+      const uint32_t n = total - off < 32768u ? total - off : 32768u;
+      bulk_g2s(slab_base() + s.sp + off, src + off, n, &c->mbar);
+    }
+  }
+  s.bits |= 0x200u;
+  __syncwarp();
+  return true;
+}
+
+__device__ __forceinline__ void wait_staged(Stack &s) {
+  if (!(s.bits & 0x200u)) return;
+  s.bits &= ~0x200u;
+  Ctrl *c = ctrl();
+  const uint32_t phase = s.phase();
+  const uint64_t tmo = c->timeout_ns;
+  if (!mbar_wait(&c->mbar, phase, tmo)) {
+    mbar_wait(&c->mbar, phase, tmo);
+    set_status(s, DSR_ERR_TIMEOUT);
+  }
+  s.bits ^= 0x100u;
+}
+
+// XOR every word of a staged frame with `key` (master warp). The frame's
+// slot is reserved in 16-byte units, so the whole slot is keyed (the words
+// past `bytes` are the slot's padding).
+__device__ __forceinline__ void key_in_place(uint8_t *dst, uint32_t bytes, uint32_t key) {
+  if (key != 0) {
+    uint4 *v = reinterpret_cast<uint4 *>(dst);
+    for (uint32_t i = lane_id(); i < (bytes + 15u) / 16u; i += 32u) {
+      uint4 x = v[i];
+      x.x ^= key;
+      x.y ^= key;
+      x.z ^= key;
+      x.w ^= key;
+      v[i] = x;
+    }
+  }
+  __syncwarp();
+}
+
 // Sum of the words [0, words) of a frame (master warp; wrap-around sum, so
 // the lane split gives the same value as one thread summing in order).
 __device__ __forceinline__ uint32_t frame_sum(const uint32_t *f, uint32_t words) {
@@ -355,65 +500,73 @@ __device__ __forceinline__ uint32_t frame_sum(const uint32_t *f, uint32_t words)
 // ---------------------------------------------------------------------------
 // Fork / join (master side) and the worker state machine
 // ---------------------------------------------------------------------------
+// Every launch gives a team at least one worker warp: a team declared with
+// no workers (32 threads) runs with one extra warp and a region width of 1,
+// which is the team of one such a region has. The master never runs a body.
 template <class P>
 __device__ __forceinline__ void parallel(const Env &e, uint32_t work, uint32_t nthreads,
                                          uint32_t arg) {
-  if (team_workers() == 0) {
-    // no workers: the master runs the region as a team of one
-    __syncwarp();
-    if (lane_id() == 0)
-      for (uint32_t v = 0; v < nthreads; ++v) P::body(e, work, v, nthreads, arg);
-    __syncwarp();
-    return;
-  }
   if (lane_id() == 0) {
     Ctrl *c = ctrl();
     c->work = work;
     c->nthreads = nthreads;
     c->arg = arg;
   }
-  named_bar(kForkBar, team_threads());  // release the workers
-  named_bar(kJoinBar, team_threads());  // resume when they are done
+  named_arrive(kForkBar, team_threads());  // release the workers
+  named_bar(kJoinBar, team_threads());     // resume when they are done
 }
 
 // The worker state machine (Fig. "codegen-worker"): wait for work at the
-// fork barrier, leave on terminate, run the body if selected, join.
-template <class P>
-__device__ __forceinline__ void worker_loop(const Env &e) {
+// fork barrier, leave on terminate, run the body if selected, join. A
+// region wider than the CTA's workers runs its threads round robin on them
+// (thread v on worker v mod W); the bodies have no barriers, so any order
+// of a worker's threads is one of the region's schedules. In a batched
+// launch (kBatched) the region and team change from task to task and are
+// read from the control block at every fork.
+template <class P, bool kBatched = false>
+__device__ __forceinline__ void worker_loop(const Env &e0) {
   const uint32_t W = team_workers();
+  Env e = e0;
   for (;;) {
     named_bar(kForkBar, team_threads());
     const Ctrl *c = ctrl();
     const uint32_t work = c->work;
     if (work == kTerminate) break;
+    if (work == kCopyWork) {
+      copy_xor(c->copy_dst, c->copy_src, c->copy_bytes, c->copy_key, threadIdx.x, W);
+      named_arrive(kJoinBar, team_threads());
+      continue;
+    }
     const uint32_t n = c->nthreads, arg = c->arg;
+    if (kBatched) {
+      e.d = &c->desc;
+      e.team = c->team;
+    }
     for (uint32_t v = threadIdx.x; v < n; v += W) P::body(e, work, v, n, arg);
-    named_bar(kJoinBar, team_threads());
+    named_arrive(kJoinBar, team_threads());
   }
 }
 
 __device__ __forceinline__ void terminate_workers() {
-  if (team_workers() == 0) return;
   if (lane_id() == 0) ctrl()->work = kTerminate;
-  named_bar(kForkBar, team_threads());
+  named_arrive(kForkBar, team_threads());
 }
 
 // Team exit (master warp): unwind what an error left live, then report.
-__device__ __forceinline__ void team_report(const Env &e, dsr_team_status *st) {
-  Ctrl *c = ctrl();
-  const int32_t status = c->status;
+__device__ __forceinline__ void team_report(const Env &e, Stack &s, dsr_team_status *st) {
+  wait_staged(s);  // no bulk copy may still be landing in the slab
+  const int32_t status = s.status();
   if (status != DSR_OK) {
-    while (c->depth) {
-      pop(c->frames[c->depth - 1].ptr);
-    }
+    while (s.depth()) pop_top(s);
   }
   __syncwarp();
   if (lane_id() == 0) {
+    const Ctrl *c = ctrl();
     dsr_team_status r;
     r.status = status;
-    r.depth_final = c->depth;
-    r.hwm_bytes = c->hwm;
-    r.spill_bytes = c->spill;
+    r.depth_final = s.depth();
+    r.hwm_bytes = s.hwm;
+    r.spill_bytes = s.spill;
 #pragma unroll
     for (int k = 0; k < DSR_MAX_DEPTH; ++k) r.chk[k] = status == DSR_OK ? c->chk[k] : 0u;
     st[e.d->status_index + e.team] = r;

@@ -8,8 +8,10 @@ from typing import Optional
 
 import numpy as np
 
-from . import (TEAM_STATUS_DTYPE, dsr_create, dsr_destroy, dsr_launch_region,
-               dsr_region_extent, dsr_stack_init)
+from . import (TEAM_STATUS_DTYPE, dsr_autotune, dsr_batch_count, dsr_batch_errors,
+               dsr_batch_workspace_bytes, dsr_create, dsr_destroy, dsr_launch_batch,
+               dsr_launch_region, dsr_launch_regions, dsr_region_extent, dsr_stack_init,
+               pack_descs)
 
 
 class Runtime:
@@ -84,3 +86,45 @@ class Runtime:
     @staticmethod
     def extent(region):
         return dsr_region_extent(region)
+
+    # -- batched form ---------------------------------------------------------
+    def batch_buffers(self, workload):
+        """Device buffers of a batch: descriptors, images, output, statuses
+        and the workspace, plus the host descriptor array and team total."""
+        torch = self.torch
+        dev = "cuda:%d" % self.device
+        descs = pack_descs(workload.regions)
+        images, out, status = self.device_buffers(workload)
+        total = dsr_batch_count(descs, images.numel(), out.numel() * 4, status.numel() // 8)
+        ws = torch.empty(dsr_batch_workspace_bytes(len(descs), total), dtype=torch.uint8,
+                         device=dev)
+        descs_dev = torch.from_numpy(descs.view(np.uint8)).to(dev)
+        return dict(descs=descs, descs_dev=descs_dev, images=images, out=out, status=status,
+                    ws=ws, total=total, program=int(descs["program"][0]))
+
+    def launch_batch(self, b, tuning=None, stream=None, use_graph=False):
+        dsr_launch_batch(self.ctx, b["descs_dev"], len(b["descs"]), b["program"], b["total"],
+                         b["images"], b["out"], b["status"], b["ws"], tuning, stream, use_graph)
+
+    def autotune(self, b, stream=None):
+        return dsr_autotune(self.ctx, b["descs_dev"], len(b["descs"]), b["program"], b["total"],
+                            b["images"], b["out"], b["status"], b["ws"], stream)
+
+    def launch_regions(self, b, stream=None):
+        dsr_launch_regions(self.ctx, b["descs"], b["images"], b["out"], b["status"], stream)
+
+    def batch_errors(self, b, stream=None):
+        return dsr_batch_errors(self.ctx, b["ws"], stream)
+
+    def run_batch(self, workload, tuning=None, use_graph=False):
+        """Run a workload's regions as one batch; returns (out, statuses)."""
+        b = self.batch_buffers(workload)
+        self.launch_batch(b, tuning, use_graph=use_graph)
+        self.torch.cuda.synchronize(self.device)
+        return self.fetch(b, workload)
+
+    def fetch(self, b, workload):
+        o = b["out"].cpu().numpy()
+        if workload.out_dtype == "float32":
+            o = o.view(np.float32)
+        return o, b["status"].cpu().numpy().view(TEAM_STATUS_DTYPE)

@@ -76,7 +76,7 @@ def test_extent_matches_workloads(L):
 def test_footprint_model(L):
     r = wl.nested(teams=1024, threads=256, depth=3).regions[0]
     f = dsr.dsr_footprint_model(r, slab_bytes=3264, regs=32)
-    assert f["smem_per_team"] == 256 + 3264 and f["spill_bytes"] == 0
+    assert f["smem_per_team"] == f["ctrl_bytes"] + 3264 and f["spill_bytes"] == 0
     assert f["teams_per_sm"] == 8 and f["limit"] == 1          # 64 warps / 8
     f = dsr.dsr_footprint_model(r, slab_bytes=2176, regs=32)
     assert f["spill_bytes"] == 1088                           # third frame spills

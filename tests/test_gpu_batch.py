@@ -1,0 +1,156 @@
+"""Batched launch form on the GPU: many heterogeneous region instances in
+one persistent kernel, checked against the CPU oracle (bit for bit)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1711_10413_gb300 as dsr
+    dsr.build()
+    r = dsr.Runtime(0, slab_bytes=16384, overflow_bytes_per_team=3 * 32768, max_teams=4096)
+    yield r
+    r.close()
+
+
+def _regions_equal(work, sel, g, gs, r, rs):
+    """Compare the outputs and statuses of the selected regions."""
+    for i in sel:
+        reg = work.regions[i]
+        o0, n = reg.out_offset // 4, reg.teams * reg.team_width
+        assert np.array_equal(g[o0:o0 + n], r[o0:o0 + n]), "instance %d output" % i
+        s0 = reg.status_index
+        for f in ("status", "depth_final", "hwm_bytes", "spill_bytes", "chk"):
+            assert np.array_equal(gs[f][s0:s0 + reg.teams], rs[f][s0:s0 + reg.teams]), (i, f)
+
+
+def test_batch_small_full_parity(rt):
+    work = wl.hetero(n_instances=300, max_teams=40)
+    for tuning in [None, dict(threads=128, slab_bytes=4096), dict(threads=1024, slab_bytes=98304)]:
+        g, gs = rt.run_batch(work, tuning)
+        r, rs = oracle.run_workload(work, slab_bytes=(tuning or {}).get("slab_bytes", 16384),
+                                    overflow_bytes=3 * 32768)
+        assert np.array_equal(g, r)
+        for f in ("status", "depth_final", "hwm_bytes", "chk"):
+            assert np.array_equal(gs[f], rs[f]), f
+        assert (gs["status"] == 0).all() and (gs["depth_final"] == 0).all()
+
+
+def test_batch_config4_full_sampled(rt):
+    """10,000 instances in one persistent launch; the oracle checks a seeded
+    sample of instances plus the largest and the widest ones."""
+    work = wl.hetero(n_instances=10000)
+    b = rt.batch_buffers(work)
+    rt.launch_batch(b, dict(threads=256, slab_bytes=32768), use_graph=True)
+    rt.torch.cuda.synchronize()
+    g, gs = rt.fetch(b, work)
+    assert rt.batch_errors(b) == (0, b["total"])
+    assert (gs["status"] == 0).all() and (gs["depth_final"] == 0).all()
+    rng = np.random.default_rng(0)
+    sel = set(rng.choice(10000, 120, replace=False).tolist())
+    sizes = [sum(r.frame_bytes) * r.teams for r in work.regions]
+    sel |= set(np.argsort(sizes)[-5:].tolist())
+    sel |= set(np.argsort([r.threads for r in work.regions])[-3:].tolist())
+    r, rs = oracle.run_workload(work, slab_bytes=32768, overflow_bytes=3 * 32768,
+                                regions=sorted(sel))
+    _regions_equal(work, sorted(sel), g, gs, r, rs)
+    # hwm of every team equals its frames' reserved sizes
+    for reg in work.regions:
+        need = sum((x + 15) // 16 * 16 for x in reg.frame_bytes)
+        assert (gs["hwm_bytes"][reg.status_index: reg.status_index + reg.teams] == need).all()
+
+
+def test_batch_spills_to_overflow(rt):
+    work = wl.hetero(n_instances=200, max_teams=16)
+    g, gs = rt.run_batch(work, dict(threads=256, slab_bytes=1024))
+    r, rs = oracle.run_workload(work, slab_bytes=1024, overflow_bytes=3 * 32768)
+    assert np.array_equal(g, r)
+    assert np.array_equal(gs["spill_bytes"], rs["spill_bytes"])
+    assert gs["spill_bytes"].max() > 0
+
+
+def test_batch_graph_replay_and_reuse(rt):
+    work = wl.hetero(n_instances=100, max_teams=8)
+    b = rt.batch_buffers(work)
+    rt.launch_batch(b, None, use_graph=True)
+    rt.torch.cuda.synchronize()
+    g1 = b["out"].clone()
+    b["out"].zero_()
+    rt.launch_batch(b, None, use_graph=True)   # replay of the captured graph
+    rt.torch.cuda.synchronize()
+    assert rt.torch.equal(g1, b["out"])
+    r, _ = oracle.run_workload(work, slab_bytes=16384, overflow_bytes=3 * 32768)
+    assert np.array_equal(g1.cpu().numpy(), r)
+
+
+def test_batch_matches_per_region_launches(rt):
+    """Each instance's output is the same alone (its own launch) and in the
+    batch."""
+    work = wl.hetero(n_instances=80, max_teams=12)
+    b = rt.batch_buffers(work)
+    rt.launch_regions(b)
+    rt.torch.cuda.synchronize()
+    alone = b["out"].cpu().numpy().copy()
+    st_alone = b["status"].cpu().numpy().copy()
+    b["out"].zero_()
+    b["status"].zero_()
+    rt.launch_batch(b, dict(threads=512, slab_bytes=16384))
+    rt.torch.cuda.synchronize()
+    assert np.array_equal(alone, b["out"].cpu().numpy())
+    assert np.array_equal(st_alone, b["status"].cpu().numpy())
+
+
+def test_batch_rejects_bad_descriptors_on_device(rt):
+    import paper_1711_10413_gb300 as dsr
+    work = wl.hetero(n_instances=50, max_teams=6)
+    b = rt.batch_buffers(work)
+    descs = b["descs"].copy()
+    descs[3]["image_offset"] = 1 << 40          # past the image buffer
+    descs[7]["program"] = dsr.DSR_PROG_NESTED   # another program
+    descs[9]["frame_bytes"][0] = 6              # not a multiple of 4
+    b["descs_dev"].copy_(rt.torch.from_numpy(descs.view(np.uint8)))
+    rt.launch_batch(b)
+    rt.torch.cuda.synchronize()
+    errors, counted = rt.batch_errors(b)
+    bad = {3, 7, 9}
+    assert errors == sum(work.regions[i].teams for i in bad)
+    g, gs = rt.fetch(b, work)
+    r, rs = oracle.run_workload(work, slab_bytes=16384, overflow_bytes=3 * 32768)
+    for i, reg in enumerate(work.regions):
+        rows = gs["status"][reg.status_index: reg.status_index + reg.teams]
+        if i in bad:
+            assert (rows == dsr.DSR_ERR_INVALID).all()
+        else:
+            assert (rows == 0).all()
+    _regions_equal(work, [i for i in range(50) if i not in bad], g, gs, r, rs)
+
+
+def test_batch_other_programs(rt):
+    """The persistent kernel runs every program: nested and scalars as batches."""
+    nested = wl.nested(teams=300, threads=256, depth=3)
+    g, gs = rt.run_batch(nested, dict(threads=256, slab_bytes=4096))
+    r, rs = oracle.run_workload(nested, slab_bytes=4096)
+    assert np.array_equal(g, r) and np.array_equal(gs["chk"], rs["chk"])
+    sc = wl.scalars(n_regions=100, teams=3, threads=128)
+    g, gs = rt.run_batch(sc, dict(threads=128, slab_bytes=1024))
+    r, rs = oracle.run_workload(sc, slab_bytes=1024)
+    assert np.array_equal(g, r)
+
+
+def test_autotune_returns_fitting_shape(rt):
+    work = wl.hetero(n_instances=400, max_teams=32)
+    b = rt.batch_buffers(work)
+    best, ms = rt.autotune(b)
+    assert best["threads"] % 32 == 0 and 64 <= best["threads"] <= 1024 and ms > 0
+    rt.torch.cuda.synchronize()
+    g, gs = rt.fetch(b, work)
+    r, rs = oracle.run_workload(work, slab_bytes=best["slab_bytes"], overflow_bytes=3 * 32768)
+    assert np.array_equal(g, r)

@@ -138,7 +138,7 @@ class Region:
     @property
     def team_width(self) -> int:
         """Threads that run each parallel region: `width` when set, else W
-        (or 1 when W == 0: the master runs the region as a team of one)."""
+        (or 1 when W == 0: the region runs as a team of one)."""
         return self.width if self.width else max(self.threads - 32, 1)
 
     def as_dict(self) -> dict:

@@ -43,6 +43,7 @@ extern "C" {
 #define DSR_MAX_DEPTH 4      /* frame sizes one region descriptor carries */
 #define DSR_MAX_FRAMES 8     /* frame-table entries per team stack */
 #define DSR_MAX_THREADS 1024 /* threads per team, master warp included */
+#define DSR_PENDING (-1)     /* dsr_serve_poll: the request has not completed */
 
 typedef enum dsr_status {
   DSR_OK = 0,
@@ -272,6 +273,79 @@ int32_t dsr_launch_regions(dsr_ctx *ctx, const dsr_region_desc *descs_host, uint
                            const void *images_dev, uint64_t image_bytes, void *out_dev,
                            uint64_t out_bytes, dsr_team_status *status_dev, uint64_t n_status,
                            void *stream);
+
+/* ---- served form: a device-resident request loop ------------------------ */
+
+/* A server: one persistent kernel that keeps every CTA's stack live and runs
+ * submitted region instances team by team as CTAs free up (continuous
+ * batching). All requests share the buffers named here; each request's
+ * descriptor offsets index them. */
+typedef struct dsr_serve_cfg {
+  uint32_t program;          /* DSR_PROG_SCALARS, _NESTED or _HETERO */
+  uint32_t threads;          /* server CTA threads, multiple of 32 in [64, 1024] */
+  uint32_t slab_bytes;       /* shared-memory slab per CTA, multiple of 16 */
+  uint32_t ctas_per_sm;      /* 0 = as many as fit */
+  uint32_t capacity;         /* requests in flight at most (ring slots), <= 2^24 */
+  uint32_t reserved;         /* 0 */
+  uint64_t idle_timeout_ns;  /* a CTA with no work for this long leaves; 0 = 2 s */
+  const void *images_dev;
+  uint64_t image_bytes;
+  void *out_dev;
+  uint64_t out_bytes;
+  dsr_team_status *status_dev;
+  uint64_t n_status;
+} dsr_serve_cfg;
+
+/* Device workspace of a server with `capacity` request slots. */
+uint64_t dsr_serve_workspace_bytes(uint32_t capacity);
+
+/* Start serving: allocates the pinned request and completion rings (host
+ * memory mapped into the device, owned by the ctx) and launches the server
+ * kernel on a ctx-owned stream. Overflow slabs come from the ctx's pool, one
+ * per server CTA. Every device-side wait of the server is bounded; a server
+ * idle for idle_timeout_ns exits and is started again by the next submit or
+ * poll. Errors: DSR_ERR_INVALID, DSR_ERR_BUDGET (workspace), DSR_ERR_CUDA. */
+int32_t dsr_serve_start(dsr_ctx *ctx, const dsr_serve_cfg *cfg, void *workspace_dev,
+                        uint64_t workspace_bytes);
+
+/* Submit one region instance (non-blocking). The descriptor is checked on
+ * the host. Admission: the request needs a free ring slot and, for its
+ * teams' frames that do not fit the server's slab, overflow bytes
+ * (spill per team x min(teams, server CTAs)) within the pool; otherwise
+ * DSR_ERR_BUDGET (try again after completions). A team that could never fit
+ * slab + its CTA's overflow slab is refused with DSR_ERR_OVERFLOW.
+ * *ticket receives the request's number. */
+int32_t dsr_serve_submit(dsr_ctx *ctx, const dsr_region_desc *d, uint64_t *ticket);
+
+/* Completion of a ticket: *status = DSR_PENDING, or the worst status of the
+ * request's teams once it completed (reported once per ticket). */
+int32_t dsr_serve_poll(dsr_ctx *ctx, uint64_t ticket, int32_t *status);
+
+/* Drain and stop: the server finishes every submitted request and exits;
+ * blocks until it has. The rings stay for a later dsr_serve_start. */
+int32_t dsr_serve_stop(dsr_ctx *ctx);
+
+/* Counters: requests submitted and completed, server CTAs that left on the
+ * idle timeout, teams rejected on the device. */
+int32_t dsr_serve_stats(dsr_ctx *ctx, uint64_t *submitted, uint64_t *completed,
+                        uint32_t *idle_exits, uint32_t *errors);
+
+/* Open-loop latency run on a started server: request i is submitted at
+ * arrival_ns[i] (nanoseconds from a start 1 ms after the call; a full ring
+ * delays submission), and latency_ns[i] = the time its completion was seen
+ * minus arrival_ns[i] (negative: -2 - status for a failed request).
+ * *elapsed_ns = start to last completion. Runs on the calling thread. */
+int32_t dsr_serve_bench(dsr_ctx *ctx, const dsr_region_desc *descs, uint32_t n,
+                        const int64_t *arrival_ns, int64_t *latency_ns, int64_t *elapsed_ns);
+
+/* The same arrivals served by one plain launch per request on `stream`
+ * (completion seen through an event per request): the per-region launch
+ * baseline of the served form. The server must not be running. */
+int32_t dsr_launch_bench(dsr_ctx *ctx, const dsr_region_desc *descs, uint32_t n,
+                         const int64_t *arrival_ns, int64_t *latency_ns, int64_t *elapsed_ns,
+                         const void *images_dev, uint64_t image_bytes, void *out_dev,
+                         uint64_t out_bytes, dsr_team_status *status_dev, uint64_t n_status,
+                         void *stream);
 
 #ifdef __cplusplus
 }

@@ -21,6 +21,7 @@ DSR_OK, DSR_ERR_INVALID, DSR_ERR_OVERFLOW, DSR_ERR_LIFO = 0, 1, 2, 3
 DSR_ERR_BUDGET, DSR_ERR_TIMEOUT, DSR_ERR_CUDA = 4, 5, 6
 DSR_MAX_DEPTH = 4
 DSR_MAX_FRAMES = 8
+DSR_PENDING = -1
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OVERFLOW", 3: "LIFO", 4: "BUDGET", 5: "TIMEOUT",
                 6: "CUDA"}
 
@@ -49,6 +50,16 @@ class dsr_config(ctypes.Structure):
 class dsr_batch_tuning(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_uint32), ("slab_bytes", ctypes.c_uint32),
                 ("ctas_per_sm", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class dsr_serve_cfg(ctypes.Structure):
+    _fields_ = [("program", ctypes.c_uint32), ("threads", ctypes.c_uint32),
+                ("slab_bytes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("capacity", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("idle_timeout_ns", ctypes.c_uint64), ("images_dev", ctypes.c_void_p),
+                ("image_bytes", ctypes.c_uint64), ("out_dev", ctypes.c_void_p),
+                ("out_bytes", ctypes.c_uint64), ("status_dev", ctypes.c_void_p),
+                ("n_status", ctypes.c_uint64)]
 
 
 class dsr_footprint(ctypes.Structure):
@@ -101,6 +112,15 @@ def _declare(L):
         "dsr_autotune": (_i32, [_vp, _vp, _u32, _u32, _u64, _vp, _u64, _vp, _u64, _vp, _u64, _vp,
                                 _u64, _vp, P(dsr_batch_tuning), P(ctypes.c_float)]),
         "dsr_launch_regions": (_i32, [_vp, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u64, _vp]),
+        "dsr_serve_workspace_bytes": (_u64, [_u32]),
+        "dsr_serve_start": (_i32, [_vp, P(dsr_serve_cfg), _vp, _u64]),
+        "dsr_serve_submit": (_i32, [_vp, P(dsr_region_desc), P(_u64)]),
+        "dsr_serve_poll": (_i32, [_vp, _u64, P(_i32)]),
+        "dsr_serve_stop": (_i32, [_vp]),
+        "dsr_serve_stats": (_i32, [_vp, P(_u64), P(_u64), P(_u32), P(_u32)]),
+        "dsr_serve_bench": (_i32, [_vp, _vp, _u32, _vp, _vp, P(ctypes.c_int64)]),
+        "dsr_launch_bench": (_i32, [_vp, _vp, _u32, _vp, _vp, P(ctypes.c_int64), _vp, _u64, _vp,
+                                    _u64, _vp, _u64, _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -129,7 +149,9 @@ def exported_symbols():
             "dsr_validate_region", "dsr_region_extent", "dsr_footprint_model",
             "dsr_launch_region", "dsr_run_region_host", "dsr_batch_workspace_bytes",
             "dsr_batch_count", "dsr_launch_batch", "dsr_batch_errors", "dsr_autotune",
-            "dsr_launch_regions"]
+            "dsr_launch_regions", "dsr_serve_workspace_bytes", "dsr_serve_start",
+            "dsr_serve_submit", "dsr_serve_poll", "dsr_serve_stop", "dsr_serve_stats",
+            "dsr_serve_bench", "dsr_launch_bench"]
 
 
 # ---------------------------------------------------------------------------
@@ -315,6 +337,71 @@ def dsr_launch_regions(ctx: int, descs: np.ndarray, images, out, status, stream=
                                     _nbytes(images) if images is not None else 0, _ptr(out),
                                     _nbytes(out), _ptr(status), _nbytes(status) // 32,
                                     _stream(stream)), ctx)
+
+
+def dsr_serve_workspace_bytes(capacity: int) -> int:
+    return int(lib().dsr_serve_workspace_bytes(capacity))
+
+
+def dsr_serve_start(ctx: int, program: int, images, out, status, workspace, threads: int = 128,
+                    slab_bytes: int = 16384, capacity: int = 4096, ctas_per_sm: int = 0,
+                    idle_timeout_ns: int = 0) -> None:
+    cfg = dsr_serve_cfg(program, threads, slab_bytes, ctas_per_sm, capacity, 0, idle_timeout_ns,
+                        _ptr(images), _nbytes(images) if images is not None else 0, _ptr(out),
+                        _nbytes(out), _ptr(status), _nbytes(status) // 32)
+    _check(lib().dsr_serve_start(ctx, ctypes.byref(cfg), _ptr(workspace), _nbytes(workspace)),
+           ctx)
+
+
+def dsr_serve_submit(ctx: int, region):
+    """Returns the ticket, or None when admission must wait (DSR_ERR_BUDGET)."""
+    d = pack_desc(region)
+    t = _u64()
+    rc = lib().dsr_serve_submit(ctx, ctypes.byref(d), ctypes.byref(t))
+    if rc == DSR_ERR_BUDGET:
+        return None
+    _check(rc, ctx)
+    return t.value
+
+
+def dsr_serve_poll(ctx: int, ticket: int) -> int:
+    st = _i32()
+    _check(lib().dsr_serve_poll(ctx, ticket, ctypes.byref(st)), ctx)
+    return st.value
+
+
+def dsr_serve_stop(ctx: int) -> None:
+    _check(lib().dsr_serve_stop(ctx), ctx)
+
+
+def dsr_serve_stats(ctx: int) -> dict:
+    a, b, c, d = _u64(), _u64(), _u32(), _u32()
+    _check(lib().dsr_serve_stats(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                 ctypes.byref(d)), ctx)
+    return dict(submitted=a.value, completed=b.value, idle_exits=c.value, errors=d.value)
+
+
+def dsr_serve_bench(ctx: int, descs: np.ndarray, arrival_ns: np.ndarray):
+    """Open-loop run on a started server; returns (latency_ns[], elapsed_ns)."""
+    arr = np.ascontiguousarray(arrival_ns, dtype=np.int64)
+    lat = np.zeros(len(descs), dtype=np.int64)
+    el = ctypes.c_int64()
+    _check(lib().dsr_serve_bench(ctx, descs.ctypes.data, len(descs), arr.ctypes.data,
+                                 lat.ctypes.data, ctypes.byref(el)), ctx)
+    return lat, el.value
+
+
+def dsr_launch_bench(ctx: int, descs: np.ndarray, arrival_ns: np.ndarray, images, out, status,
+                     stream=None):
+    arr = np.ascontiguousarray(arrival_ns, dtype=np.int64)
+    lat = np.zeros(len(descs), dtype=np.int64)
+    el = ctypes.c_int64()
+    _check(lib().dsr_launch_bench(ctx, descs.ctypes.data, len(descs), arr.ctypes.data,
+                                  lat.ctypes.data, ctypes.byref(el), _ptr(images),
+                                  _nbytes(images) if images is not None else 0, _ptr(out),
+                                  _nbytes(out), _ptr(status), _nbytes(status) // 32,
+                                  _stream(stream)), ctx)
+    return lat, el.value
 
 
 from .runtime import Runtime  # noqa: E402  (convenience wrapper over the calls above)

@@ -1,12 +1,694 @@
-// dsr_serve.cu -- served launch form (device-resident request loop).
+// dsr_serve.cu -- served launch form: a device-resident request loop.
+//
+// A persistent server kernel keeps every CTA's team stack live on the GPU
+// and runs region instances as the host submits them, without a kernel
+// launch per request: continuous batching. Requests that arrive while
+// others run are picked up team by team as CTAs free up, so different
+// requests' teams share the GPU at the same time.
+//
+// Host <-> device protocol, in pinned host memory mapped into the device:
+//  * submit ring: `capacity` descriptor slots and a tail counter. The host
+//    writes request s into slot s % capacity and then stores tail = s + 1
+//    with release order; the device reads the tail with a system-scope
+//    acquire load before it reads the slot.
+//  * completion ring: records {s + 1, status} the device writes (payload
+//    first, then the marker with a system-scope release store) at
+//    positions it takes from a device counter; the host consumes them in
+//    position order and clears each.
+//  * stop flag: set by the host; the server drains what was submitted and
+//    exits.
+// Device workspace (caller-owned): the head of the request stream and, per
+// slot, a claim word (request sequence << 32 | next team) and counters of
+// finished teams and the worst team status. A CTA claims a team with one
+// 64-bit atomic add on the claim word and keeps it only when the sequence
+// half still names the request it read, so a slot reused for a later
+// request is never mistaken for an earlier one.
+// Only one CTA, the doorbell, reads host memory: it copies the tail and the
+// stop flag into device memory, where the other CTAs poll with backoff, so
+// idle CTAs do not flood the host memory with reads.
+// Every device-side wait is bounded: a CTA that finds no work for
+// idle_timeout_ns leaves (the host restarts the server on the next submit
+// or poll).
 #include <cuda_runtime.h>
 
-#include "dsr.h"
-#include "dsr_ctx.h"
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <thread>
+#include <unordered_map>
+#include <vector>
 
-struct dsr_serve_state {};
+#include "dsr.h"
+#include "dsr_check.cuh"
+#include "dsr_ctx.h"
+#include "dsr_programs.cuh"
+
+using namespace dsr;
+
+namespace {
+
+struct alignas(16) CompRec {
+  unsigned long long marker;  // request sequence + 1; 0 = empty
+  int status;
+  unsigned int pad;
+};
+
+struct HostShared {  // pinned, mapped
+  unsigned long long tail;  // requests published
+  unsigned long long stop;  // 1 = drain and exit
+  unsigned long long pad[14];
+};
+
+struct alignas(16) SlotState {
+  unsigned long long claim;  // (sequence << 32) | next team to hand out
+  unsigned int done;         // teams finished
+  int status;                // worst team status
+};
+
+struct ServeWs {  // device workspace header
+  unsigned long long head;       // oldest request that may still have unclaimed teams
+  unsigned long long comp_tail;  // completion records written
+  unsigned long long tail;       // the doorbell's copy of the host's tail
+  unsigned long long stop;       // the doorbell's copy of the host's stop flag
+  unsigned int idle_exits;       // CTAs that left after the idle timeout
+  unsigned int errors;           // teams rejected on the device
+  unsigned int pad[22];
+};
+
+struct ServeArgs {
+  const dsr_region_desc *ring;  // device view of the submit ring
+  HostShared *hs;               // device view
+  CompRec *comp;                // device view of the completion ring
+  ServeWs *ws;
+  SlotState *slots;
+  const uint8_t *images;
+  uint8_t *out;
+  dsr_team_status *status;
+  uint8_t *pool;
+  uint64_t image_bytes;
+  uint64_t out_bytes;
+  uint64_t n_status;
+  uint64_t ovf_per_cta;
+  uint64_t timeout_ns;       // bound on fills
+  uint64_t idle_timeout_ns;  // leave after this long without work
+  uint32_t capacity;         // submit-ring slots (completion ring: same)
+  uint32_t slab_bytes;
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_gpu(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_sys(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Claim one team of a submitted request (master warp). Returns false when
+// no team is available now.
+__device__ __forceinline__ bool claim(const ServeArgs &a, unsigned long long *seq,
+                                      uint32_t *team) {
+  unsigned long long out_seq = 0;
+  uint32_t out_team = 0, got = 0;
+  if (lane_id() == 0) {
+    for (int tries = 0; tries < 64 && !got; ++tries) {
+      const unsigned long long h = ld_relaxed_gpu(&a.ws->head);
+      const unsigned long long tail = ld_acquire_gpu(&a.ws->tail);
+      if (h >= tail) break;
+      const uint32_t slot = static_cast<uint32_t>(h % a.capacity);
+      const uint32_t T = a.ring[slot].teams;
+      unsigned long long w = ld_relaxed_gpu(&a.slots[slot].claim);
+      bool advance = false;
+      for (int cas = 0; cas < 32; ++cas) {
+        if ((w >> 32) != (h & 0xffffffffull) || static_cast<uint32_t>(w) >= T) {
+          advance = true;  // h's teams are all handed out, or h is done
+          break;
+        }
+        const unsigned long long prev = atomicCAS(&a.slots[slot].claim, w, w + 1);
+        if (prev == w) {
+          got = 1;
+          out_seq = h;
+          out_team = static_cast<uint32_t>(w);
+          break;
+        }
+        w = prev;
+      }
+      if (advance) atomicCAS(&a.ws->head, h, h + 1);
+    }
+  }
+  got = __shfl_sync(0xffffffffu, got, 0);
+  *seq = __shfl_sync(0xffffffffu, out_seq, 0);
+  *team = __shfl_sync(0xffffffffu, out_team, 0);
+  return got != 0;
+}
+
+template <class P, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) serve_kernel(const __grid_constant__ ServeArgs a) {
+  Env e;
+  e.d = nullptr;
+  e.images = a.images;
+  e.out = a.out;
+  e.team = 0;
+  if (threadIdx.x < team_workers()) {
+    worker_loop<P, true>(e);
+    return;
+  }
+  const uint32_t lane = lane_id();
+  if (blockIdx.x == gridDim.x - 1) {
+    // The doorbell: the only reader of host memory. It copies the host's
+    // tail (and stop flag) into device memory, where the other CTAs poll,
+    // and leaves on stop or after idle_timeout_ns without a new request.
+    if (lane == 0) {
+      unsigned long long last = ld_relaxed_gpu(&a.ws->tail);
+      uint64_t idle_since = globaltimer();
+      for (;;) {
+        const unsigned long long stop = ld_acquire_sys(&a.hs->stop);
+        const unsigned long long t = ld_acquire_sys(&a.hs->tail);
+        if (t != last) {
+          st_release_gpu(&a.ws->tail, t);
+          last = t;
+          idle_since = globaltimer();
+        }
+        if (stop) {
+          st_release_gpu(&a.ws->stop, 1ull);
+          break;
+        }
+        if (globaltimer() - idle_since > a.idle_timeout_ns) {
+          atomicAdd(&a.ws->idle_exits, 1u);
+          break;
+        }
+        __nanosleep(256);
+      }
+    }
+    __syncwarp();
+    terminate_workers();
+    return;
+  }
+  Ctrl *c = ctrl();
+  Stack s;
+  uint8_t *ovf = a.ovf_per_cta ? a.pool + static_cast<uint64_t>(blockIdx.x) * a.ovf_per_cta : nullptr;
+  bool first = true;
+  uint64_t idle_since = globaltimer();
+  uint32_t backoff = 256;
+  for (;;) {
+    unsigned long long seq;
+    uint32_t team;
+    if (!claim(a, &seq, &team)) {
+      // nothing to run: leave when asked to stop (all submitted work has
+      // been claimed) or after the idle timeout; otherwise back off
+      unsigned long long stop = 0;
+      if (lane == 0) stop = ld_acquire_gpu(&a.ws->stop);
+      stop = __shfl_sync(0xffffffffu, stop, 0);
+      if (stop) break;
+      if (globaltimer() - idle_since > a.idle_timeout_ns) {
+        if (lane == 0) atomicAdd(&a.ws->idle_exits, 1u);
+        break;
+      }
+      __nanosleep(backoff);
+      backoff = backoff < 4096 ? backoff * 2 : 4096;
+      continue;
+    }
+    backoff = 256;
+    idle_since = globaltimer();
+    const uint32_t slot = static_cast<uint32_t>(seq % a.capacity);
+    __syncwarp();
+    if (lane < 4)
+      reinterpret_cast<uint4 *>(&c->desc)[lane] =
+          reinterpret_cast<const uint4 *>(a.ring + slot)[lane];
+    if (lane == 0) c->team = team;
+    __syncwarp();
+    e.d = &c->desc;
+    e.team = team;
+    team_setup(s, a.slab_bytes, ovf, a.ovf_per_cta, a.timeout_ns, first);
+    first = false;
+    const dsr_region_desc &d = c->desc;
+    int32_t st;
+    if (d.program != P::kProgram || shape_error(d) != 0 ||
+        !fits(d, a.image_bytes, a.out_bytes, a.n_status)) {
+      st = DSR_ERR_INVALID;
+      if (lane == 0) {
+        atomicAdd(&a.ws->errors, 1u);
+        const uint64_t si = static_cast<uint64_t>(d.status_index) + team;
+        if (si < a.n_status) {
+          dsr_team_status r = {};
+          r.status = DSR_ERR_INVALID;
+          a.status[si] = r;
+        }
+      }
+    } else {
+      P::master(e, s);
+      st = s.status();
+      team_report(e, s, a.status);
+    }
+    if (lane == 0) {
+      __threadfence();  // this team's outputs before its completion count
+      if (st != DSR_OK) atomicMax(&a.slots[slot].status, st);
+      const uint32_t done = atomicAdd(&a.slots[slot].done, 1u) + 1u;
+      if (done == d.teams) {
+        // the request's last team: recycle the slot for request seq +
+        // capacity, then publish the completion to the host
+        __threadfence();
+        const int rst = atomicAdd(&a.slots[slot].status, 0);
+        a.slots[slot].done = 0;
+        a.slots[slot].status = 0;
+        __threadfence();
+        atomicExch(&a.slots[slot].claim, ((seq + a.capacity) & 0xffffffffull) << 32);
+        const unsigned long long pos = atomicAdd(&a.ws->comp_tail, 1ull);
+        CompRec *r = a.comp + (pos % a.capacity);
+        r->status = rst;
+        __threadfence_system();
+        st_release_sys(&r->marker, seq + 1);
+      }
+    }
+    __syncwarp();
+  }
+  terminate_workers();
+}
+
+using ServeFn = void (*)(ServeArgs);
+
+template <class P>
+ServeFn pick_serve(uint32_t threads) {
+  if (threads <= 128) return serve_kernel<P, 128, 12>;
+  if (threads <= 256) return serve_kernel<P, 256, 4>;
+  return serve_kernel<P, 1024, 1>;
+}
+
+ServeFn serve_kernel_for(uint32_t program, uint32_t threads) {
+  switch (program) {
+    case DSR_PROG_SCALARS: return pick_serve<ProgScalars>(threads);
+    case DSR_PROG_NESTED: return pick_serve<ProgNested>(threads);
+    case DSR_PROG_HETERO: return pick_serve<ProgHetero>(threads);
+    default: return nullptr;
+  }
+}
+
+uint64_t serve_ws_bytes(uint32_t capacity) {
+  return sizeof(ServeWs) + sizeof(SlotState) * static_cast<uint64_t>(capacity);
+}
+
+__global__ void serve_init(ServeWs *ws, SlotState *slots, uint32_t capacity) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    ws->head = 0;
+    ws->comp_tail = 0;
+    ws->tail = 0;
+    ws->stop = 0;
+    ws->idle_exits = 0;
+    ws->errors = 0;
+  }
+  if (i < capacity) {
+    slots[i].claim = static_cast<unsigned long long>(i) << 32;
+    slots[i].done = 0;
+    slots[i].status = 0;
+  }
+}
+
+// Before a server starts again (after a stop or an idle exit): clear the
+// stop copy; the head, tail copy and completion counters continue.
+__global__ void serve_reopen(ServeWs *ws) {
+  ws->stop = 0;
+  ws->idle_exits = 0;
+}
+
+}  // namespace
+
+struct dsr_serve_state {
+  dsr_serve_cfg cfg{};
+  uint32_t grid = 0;
+  cudaStream_t stream = nullptr;
+  bool running = false;
+  bool launched = false;
+  // pinned, mapped host memory
+  dsr_region_desc *ring = nullptr;
+  HostShared *hs = nullptr;
+  CompRec *comp = nullptr;
+  dsr_region_desc *ring_dev = nullptr;
+  HostShared *hs_dev = nullptr;
+  CompRec *comp_dev = nullptr;
+  // device workspace (caller-owned)
+  ServeWs *ws = nullptr;
+  SlotState *slots = nullptr;
+  // host bookkeeping
+  uint64_t next_seq = 0;       // next ticket
+  uint64_t comp_pos = 0;       // next completion record to read
+  uint64_t completed = 0;      // requests completed
+  std::unordered_map<uint64_t, int32_t> done;  // ticket -> status, until polled
+  std::vector<uint8_t> slot_busy;               // slot holds an unfinished request
+  std::unordered_map<uint64_t, uint64_t> reserved;  // ticket -> overflow bytes reserved
+  uint64_t reserved_bytes = 0;
+  uint64_t pool_budget = 0;
+};
 
 void dsr_serve_release(dsr_ctx *ctx) {
-  delete ctx->serve;
+  dsr_serve_state *sv = ctx->serve;
+  if (!sv) return;
+  if (sv->running) dsr_serve_stop(ctx);
+  if (sv->stream) cudaStreamDestroy(sv->stream);
+  if (sv->ring) cudaFreeHost(sv->ring);
+  if (sv->hs) cudaFreeHost(sv->hs);
+  if (sv->comp) cudaFreeHost(sv->comp);
+  delete sv;
   ctx->serve = nullptr;
+}
+
+namespace {
+
+int32_t launch_server(dsr_ctx *ctx, dsr_serve_state *sv) {
+  if (sv->launched) serve_reopen<<<1, 1, 0, sv->stream>>>(sv->ws);
+  sv->launched = true;
+  ServeArgs a;
+  a.ring = sv->ring_dev;
+  a.hs = sv->hs_dev;
+  a.comp = sv->comp_dev;
+  a.ws = sv->ws;
+  a.slots = sv->slots;
+  a.images = static_cast<const uint8_t *>(sv->cfg.images_dev);
+  a.out = static_cast<uint8_t *>(sv->cfg.out_dev);
+  a.status = sv->cfg.status_dev;
+  a.pool = ctx->pool;
+  a.image_bytes = sv->cfg.image_bytes;
+  a.out_bytes = sv->cfg.out_bytes;
+  a.n_status = sv->cfg.n_status;
+  a.ovf_per_cta = ctx->ovf_per_team;
+  a.timeout_ns = ctx->timeout_ns;
+  a.idle_timeout_ns = sv->cfg.idle_timeout_ns ? sv->cfg.idle_timeout_ns : 2000000000ull;
+  a.capacity = sv->cfg.capacity;
+  a.slab_bytes = sv->cfg.slab_bytes;
+  serve_kernel_for(sv->cfg.program, sv->cfg.threads)<<<sv->grid, sv->cfg.threads,
+                                                        kCtrlBytes + sv->cfg.slab_bytes,
+                                                        sv->stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "server launch");
+  sv->running = true;
+  return DSR_OK;
+}
+
+// Overflow bytes one team of `d` may hold at once, with the server's slab.
+uint64_t team_spill(const dsr_region_desc &d, uint32_t slab) {
+  uint64_t sp = 0, spill = 0;
+  for (uint32_t k = 0; k < d.depth; ++k) {
+    const uint64_t fp = pad16(d.frame_bytes[k]);
+    if (sp + fp <= slab)
+      sp += fp;
+    else
+      spill += fp;
+  }
+  return spill;
+}
+
+// Read new completion records (host side): free their slots and their
+// overflow reservations.
+void drain_completions(dsr_serve_state *sv) {
+  for (;;) {
+    CompRec *r = sv->comp + (sv->comp_pos % sv->cfg.capacity);
+    const unsigned long long m = __atomic_load_n(&r->marker, __ATOMIC_ACQUIRE);
+    if (m == 0) break;
+    const uint64_t seq = m - 1;
+    sv->done[seq] = r->status;
+    __atomic_store_n(&r->marker, 0ull, __ATOMIC_RELAXED);
+    ++sv->comp_pos;
+    ++sv->completed;
+    sv->slot_busy[seq % sv->cfg.capacity] = 0;
+    auto it = sv->reserved.find(seq);
+    if (it != sv->reserved.end()) {
+      sv->reserved_bytes -= it->second;
+      sv->reserved.erase(it);
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" uint64_t dsr_serve_workspace_bytes(uint32_t capacity) { return serve_ws_bytes(capacity); }
+
+extern "C" int32_t dsr_serve_start(dsr_ctx *ctx, const dsr_serve_cfg *cfg, void *workspace_dev,
+                                   uint64_t workspace_bytes) {
+  if (!ctx || !cfg) return dsr_fail(ctx, DSR_ERR_INVALID, "null argument");
+  if (!ctx->stack_ready) return dsr_fail(ctx, DSR_ERR_INVALID, "dsr_stack_init not called");
+  if (ctx->serve && ctx->serve->running) return dsr_fail(ctx, DSR_ERR_INVALID, "already serving");
+  if (!serve_kernel_for(cfg->program, cfg->threads))
+    return dsr_fail(ctx, DSR_ERR_INVALID, "the served form runs the scalars, nested and hetero programs");
+  if (cfg->threads < 64 || cfg->threads > DSR_MAX_THREADS || cfg->threads % 32 ||
+      cfg->slab_bytes % 16 || kCtrlBytes + cfg->slab_bytes > static_cast<uint32_t>(ctx->max_smem_optin) ||
+      cfg->capacity == 0 || cfg->capacity > (1u << 24) || !cfg->out_dev || !cfg->status_dev)
+    return dsr_fail(ctx, DSR_ERR_INVALID, "bad serve configuration");
+  if (!workspace_dev || (reinterpret_cast<uintptr_t>(workspace_dev) & 15u) ||
+      workspace_bytes < serve_ws_bytes(cfg->capacity))
+    return dsr_fail(ctx, DSR_ERR_BUDGET, "serve workspace needs %llu bytes, 16-byte aligned",
+                    (unsigned long long)serve_ws_bytes(cfg->capacity));
+  dsr_serve_release(ctx);
+  dsr_serve_state *sv = new dsr_serve_state();
+  ctx->serve = sv;
+  sv->cfg = *cfg;
+  cudaError_t e;
+  const unsigned fl = cudaHostAllocMapped | cudaHostAllocPortable;
+  if ((e = cudaHostAlloc(&sv->ring, sizeof(dsr_region_desc) * cfg->capacity, fl)) != cudaSuccess ||
+      (e = cudaHostAlloc(&sv->hs, sizeof(HostShared), fl)) != cudaSuccess ||
+      (e = cudaHostAlloc(&sv->comp, sizeof(CompRec) * cfg->capacity, fl)) != cudaSuccess ||
+      (e = cudaHostGetDevicePointer(&sv->ring_dev, sv->ring, 0)) != cudaSuccess ||
+      (e = cudaHostGetDevicePointer(&sv->hs_dev, sv->hs, 0)) != cudaSuccess ||
+      (e = cudaHostGetDevicePointer(&sv->comp_dev, sv->comp, 0)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+    int32_t rc = dsr_cuda_fail(ctx, e, "serve rings");
+    dsr_serve_release(ctx);
+    return rc;
+  }
+  std::memset(sv->ring, 0, sizeof(dsr_region_desc) * cfg->capacity);
+  std::memset(sv->hs, 0, sizeof(HostShared));
+  std::memset(sv->comp, 0, sizeof(CompRec) * cfg->capacity);
+  sv->slot_busy.assign(cfg->capacity, 0);
+  sv->ws = static_cast<ServeWs *>(workspace_dev);
+  sv->slots = reinterpret_cast<SlotState *>(static_cast<uint8_t *>(workspace_dev) + sizeof(ServeWs));
+  ServeFn k = serve_kernel_for(cfg->program, cfg->threads);
+  if ((e = cudaFuncSetAttribute(reinterpret_cast<const void *>(k),
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                ctx->max_smem_optin)) != cudaSuccess) {
+    int32_t rc = dsr_cuda_fail(ctx, e, "serve attributes");
+    dsr_serve_release(ctx);
+    return rc;
+  }
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, reinterpret_cast<const void *>(k),
+                                                cfg->threads, kCtrlBytes + cfg->slab_bytes);
+  if (occ < 1) {
+    dsr_serve_release(ctx);
+    return dsr_fail(ctx, DSR_ERR_INVALID, "serve CTA shape does not fit an SM");
+  }
+  uint64_t g = static_cast<uint64_t>(ctx->sm_count) *
+               (cfg->ctas_per_sm ? std::min<uint32_t>(cfg->ctas_per_sm, occ) : occ);
+  if (ctx->ovf_per_team) g = std::min<uint64_t>(g, ctx->max_teams);
+  if (g < 2) {
+    dsr_serve_release(ctx);
+    return dsr_fail(ctx, DSR_ERR_BUDGET, "a server needs two CTAs (the doorbell and one more)");
+  }
+  sv->grid = static_cast<uint32_t>(g);
+  sv->pool_budget = ctx->ovf_per_team * g;
+  serve_init<<<(cfg->capacity + 255) / 256, 256, 0, sv->stream>>>(sv->ws, sv->slots, cfg->capacity);
+  int32_t rc = launch_server(ctx, sv);
+  if (rc != DSR_OK) dsr_serve_release(ctx);
+  return rc;
+}
+
+extern "C" int32_t dsr_serve_submit(dsr_ctx *ctx, const dsr_region_desc *d, uint64_t *ticket) {
+  if (!ctx || !ctx->serve || !d || !ticket) return dsr_fail(ctx, DSR_ERR_INVALID, "not serving");
+  dsr_serve_state *sv = ctx->serve;
+  if (d->program != sv->cfg.program) return dsr_fail(ctx, DSR_ERR_INVALID, "program mismatch");
+  int32_t rc = dsr_validate_region(d, sv->cfg.image_bytes, sv->cfg.out_bytes, sv->cfg.n_status);
+  if (rc != DSR_OK) return dsr_fail(ctx, rc, "%s", dsr_last_error_string(nullptr));
+  const uint64_t spill = team_spill(*d, sv->cfg.slab_bytes);
+  if (spill > ctx->ovf_per_team)
+    return dsr_fail(ctx, DSR_ERR_OVERFLOW, "a team needs %llu overflow bytes, %llu per CTA",
+                    (unsigned long long)spill, (unsigned long long)ctx->ovf_per_team);
+  drain_completions(sv);
+  // admission: the request's ring slot is free (its previous occupant has
+  // completed), and its overflow reservation fits the pool
+  if (sv->slot_busy[sv->next_seq % sv->cfg.capacity])
+    return dsr_fail(ctx, DSR_ERR_BUDGET, "request ring full");
+  const uint64_t want = spill * std::min<uint64_t>(d->teams, sv->grid);
+  if (sv->reserved_bytes + want > sv->pool_budget)
+    return dsr_fail(ctx, DSR_ERR_BUDGET, "overflow pool budget in use");
+  // a server that left after its idle timeout is started again
+  if (sv->running && cudaStreamQuery(sv->stream) == cudaSuccess) sv->running = false;
+  if (!sv->running && (rc = launch_server(ctx, sv)) != DSR_OK) return rc;
+  const uint64_t seq = sv->next_seq++;
+  sv->ring[seq % sv->cfg.capacity] = *d;
+  sv->slot_busy[seq % sv->cfg.capacity] = 1;
+  if (want) {
+    sv->reserved[seq] = want;
+    sv->reserved_bytes += want;
+  }
+  __atomic_store_n(&sv->hs->tail, static_cast<unsigned long long>(seq + 1), __ATOMIC_RELEASE);
+  *ticket = seq;
+  return DSR_OK;
+}
+
+extern "C" int32_t dsr_serve_poll(dsr_ctx *ctx, uint64_t ticket, int32_t *status) {
+  if (!ctx || !ctx->serve || !status) return dsr_fail(ctx, DSR_ERR_INVALID, "not serving");
+  dsr_serve_state *sv = ctx->serve;
+  drain_completions(sv);
+  if (sv->running && sv->completed < sv->next_seq && cudaStreamQuery(sv->stream) == cudaSuccess) {
+    // every CTA left after the idle timeout while work was published
+    sv->running = false;
+    int32_t rc = launch_server(ctx, sv);
+    if (rc != DSR_OK) return rc;
+  }
+  auto it = sv->done.find(ticket);
+  if (it == sv->done.end()) {
+    *status = DSR_PENDING;
+    return DSR_OK;
+  }
+  *status = it->second;
+  sv->done.erase(it);
+  return DSR_OK;
+}
+
+extern "C" int32_t dsr_serve_stop(dsr_ctx *ctx) {
+  if (!ctx || !ctx->serve) return DSR_OK;
+  dsr_serve_state *sv = ctx->serve;
+  __atomic_store_n(&sv->hs->stop, 1ull, __ATOMIC_RELEASE);
+  cudaError_t e = cudaStreamSynchronize(sv->stream);
+  sv->running = false;
+  __atomic_store_n(&sv->hs->stop, 0ull, __ATOMIC_RELEASE);
+  drain_completions(sv);
+  if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "server stop");
+  return DSR_OK;
+}
+
+extern "C" int32_t dsr_serve_stats(dsr_ctx *ctx, uint64_t *submitted, uint64_t *completed,
+                                   uint32_t *idle_exits, uint32_t *errors) {
+  if (!ctx || !ctx->serve) return dsr_fail(ctx, DSR_ERR_INVALID, "not serving");
+  dsr_serve_state *sv = ctx->serve;
+  drain_completions(sv);
+  ServeWs w;
+  cudaError_t e = cudaMemcpy(&w, sv->ws, sizeof(w), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "serve stats");
+  if (submitted) *submitted = sv->next_seq;
+  if (completed) *completed = sv->completed;
+  if (idle_exits) *idle_exits = w.idle_exits;
+  if (errors) *errors = w.errors;
+  return DSR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Open-loop latency harnesses (host threads; the clock is CLOCK_MONOTONIC)
+// ---------------------------------------------------------------------------
+namespace {
+inline uint64_t now_ns() {
+  return static_cast<uint64_t>(std::chrono::duration_cast<std::chrono::nanoseconds>(
+                                   std::chrono::steady_clock::now().time_since_epoch())
+                                   .count());
+}
+}  // namespace
+
+extern "C" int32_t dsr_serve_bench(dsr_ctx *ctx, const dsr_region_desc *descs, uint32_t n,
+                                   const int64_t *arrival_ns, int64_t *latency_ns,
+                                   int64_t *elapsed_ns) {
+  if (!ctx || !ctx->serve || !descs || !arrival_ns || !latency_ns)
+    return dsr_fail(ctx, DSR_ERR_INVALID, "not serving or null argument");
+  dsr_serve_state *sv = ctx->serve;
+  std::vector<int64_t> sched(n);
+  std::vector<uint64_t> tickets(n, ~0ull);
+  std::unordered_map<uint64_t, uint32_t> by_ticket;
+  const uint64_t t0 = now_ns() + 1000000;  // start 1 ms from now
+  uint32_t next = 0, finished = 0;
+  for (uint32_t i = 0; i < n; ++i) latency_ns[i] = -1;
+  const uint64_t deadline = t0 + static_cast<uint64_t>(arrival_ns[n ? n - 1 : 0]) + 30000000000ull;
+  while (finished < n) {
+    const uint64_t now = now_ns();
+    if (now > deadline) return dsr_fail(ctx, DSR_ERR_TIMEOUT, "serve bench did not finish");
+    // submit every request whose arrival time has come (open loop: a full
+    // ring delays the submission, and that delay counts as latency)
+    while (next < n && now >= t0 + static_cast<uint64_t>(arrival_ns[next])) {
+      uint64_t tk;
+      const int32_t rc = dsr_serve_submit(ctx, descs + next, &tk);
+      if (rc == DSR_ERR_BUDGET) break;
+      if (rc != DSR_OK) return rc;
+      tickets[next] = tk;
+      by_ticket[tk] = next;
+      ++next;
+    }
+    drain_completions(sv);
+    for (auto it = sv->done.begin(); it != sv->done.end();) {
+      auto f = by_ticket.find(it->first);
+      if (f == by_ticket.end()) {
+        ++it;
+        continue;
+      }
+      latency_ns[f->second] = static_cast<int64_t>(now_ns() - (t0 + arrival_ns[f->second]));
+      if (it->second != DSR_OK) latency_ns[f->second] = -2 - it->second;
+      by_ticket.erase(f);
+      it = sv->done.erase(it);
+      ++finished;
+    }
+  }
+  if (elapsed_ns) *elapsed_ns = static_cast<int64_t>(now_ns() - t0);
+  return DSR_OK;
+}
+
+// The same open-loop arrivals served by one plain kernel launch per request
+// on `stream`; completion is observed through an event per request.
+extern "C" int32_t dsr_launch_bench(dsr_ctx *ctx, const dsr_region_desc *descs, uint32_t n,
+                                    const int64_t *arrival_ns, int64_t *latency_ns,
+                                    int64_t *elapsed_ns, const void *images_dev,
+                                    uint64_t image_bytes, void *out_dev, uint64_t out_bytes,
+                                    dsr_team_status *status_dev, uint64_t n_status,
+                                    void *stream) {
+  if (!ctx || !descs || !arrival_ns || !latency_ns)
+    return dsr_fail(ctx, DSR_ERR_INVALID, "null argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint32_t kEvents = 4096;
+  std::vector<cudaEvent_t> ev(kEvents);
+  for (auto &x : ev) cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+  std::deque<std::pair<uint32_t, uint32_t>> inflight;  // (request, event)
+  uint32_t next = 0, finished = 0, ev_next = 0;
+  const uint64_t t0 = now_ns() + 1000000;
+  const uint64_t deadline = t0 + static_cast<uint64_t>(arrival_ns[n ? n - 1 : 0]) + 60000000000ull;
+  int32_t rc = DSR_OK;
+  while (finished < n && rc == DSR_OK) {
+    const uint64_t now = now_ns();
+    if (now > deadline) {
+      rc = dsr_fail(ctx, DSR_ERR_TIMEOUT, "launch bench did not finish");
+      break;
+    }
+    while (next < n && now >= t0 + static_cast<uint64_t>(arrival_ns[next]) &&
+           inflight.size() < kEvents) {
+      rc = dsr_launch_region(ctx, descs + next, images_dev, image_bytes, out_dev, out_bytes,
+                             status_dev, n_status, stream);
+      if (rc != DSR_OK) break;
+      cudaEventRecord(ev[ev_next], s);
+      inflight.emplace_back(next, ev_next);
+      ev_next = (ev_next + 1) % kEvents;
+      ++next;
+    }
+    while (!inflight.empty() && cudaEventQuery(ev[inflight.front().second]) == cudaSuccess) {
+      const uint32_t i = inflight.front().first;
+      latency_ns[i] = static_cast<int64_t>(now_ns() - (t0 + arrival_ns[i]));
+      inflight.pop_front();
+      ++finished;
+    }
+  }
+  cudaStreamSynchronize(s);
+  for (auto &x : ev) cudaEventDestroy(x);
+  if (elapsed_ns) *elapsed_ns = static_cast<int64_t>(now_ns() - t0);
+  return rc;
 }

@@ -10,8 +10,8 @@ import numpy as np
 
 from . import (TEAM_STATUS_DTYPE, dsr_autotune, dsr_batch_count, dsr_batch_errors,
                dsr_batch_workspace_bytes, dsr_create, dsr_destroy, dsr_launch_batch,
-               dsr_launch_region, dsr_launch_regions, dsr_region_extent, dsr_stack_init,
-               pack_descs)
+               dsr_launch_region, dsr_launch_regions, dsr_region_extent, dsr_serve_start,
+               dsr_serve_stop, dsr_serve_workspace_bytes, dsr_stack_init, pack_descs)
 
 
 class Runtime:
@@ -128,3 +128,21 @@ class Runtime:
         if workload.out_dtype == "float32":
             o = o.view(np.float32)
         return o, b["status"].cpu().numpy().view(TEAM_STATUS_DTYPE)
+
+    # -- served form ----------------------------------------------------------
+    def serve_start(self, workload, threads=128, slab_bytes=16384, capacity=4096,
+                    idle_timeout_ns=0):
+        """Start a server over a workload's buffers; returns the buffer dict
+        (allocated before the server occupies the SMs)."""
+        torch = self.torch
+        dev = "cuda:%d" % self.device
+        images, out, status = self.device_buffers(workload)
+        ws = torch.empty(dsr_serve_workspace_bytes(capacity), dtype=torch.uint8, device=dev)
+        torch.cuda.synchronize(self.device)
+        program = workload.regions[0].program
+        dsr_serve_start(self.ctx, program, images, out, status, ws, threads, slab_bytes,
+                        capacity, 0, idle_timeout_ns)
+        return dict(images=images, out=out, status=status, ws=ws, descs=pack_descs(workload.regions))
+
+    def serve_stop(self):
+        dsr_serve_stop(self.ctx)

@@ -1,0 +1,160 @@
+"""Served form on the GPU: a device-resident request loop with continuous
+batching. Every request's result must equal the oracle's (and so its
+result alone), whatever else was in flight with it."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1711_10413_gb300 as dsr
+    dsr.build()
+    r = dsr.Runtime(0, slab_bytes=16384, overflow_bytes_per_team=3 * 32768, max_teams=4096)
+    yield r
+    try:
+        r.serve_stop()
+    except Exception:
+        pass
+    r.close()
+
+
+def _submit_all(dsr, rt, regions, deadline_s=30.0):
+    tickets, pending = [], list(regions)
+    t0 = time.time()
+    while pending:
+        assert time.time() - t0 < deadline_s
+        tk = dsr.dsr_serve_submit(rt.ctx, pending[0])
+        if tk is None:          # admission must wait for completions
+            dsr.dsr_serve_poll(rt.ctx, 1 << 62)
+            continue
+        tickets.append(tk)
+        pending.pop(0)
+    return tickets
+
+
+def _wait_all(dsr, rt, tickets, deadline_s=30.0):
+    st, left, t0 = {}, set(tickets), time.time()
+    while left:
+        assert time.time() - t0 < deadline_s, "requests did not complete"
+        for tk in list(left):
+            s = dsr.dsr_serve_poll(rt.ctx, tk)
+            if s != dsr.DSR_PENDING:
+                st[tk] = s
+                left.discard(tk)
+    return st
+
+
+def test_serve_mix_equals_oracle(rt):
+    import paper_1711_10413_gb300 as dsr
+    work = wl.hetero(n_instances=400, max_teams=24)
+    b = rt.serve_start(work, threads=128, slab_bytes=8192, capacity=64)
+    try:
+        tickets = _submit_all(dsr, rt, work.regions)
+        st = _wait_all(dsr, rt, tickets)
+    finally:
+        rt.serve_stop()
+    assert all(v == 0 for v in st.values())
+    g = b["out"].cpu().numpy()
+    gs = b["status"].cpu().numpy().view(dsr.TEAM_STATUS_DTYPE)
+    r, rs = oracle.run_workload(work, slab_bytes=8192, overflow_bytes=3 * 32768)
+    assert np.array_equal(g, r)
+    for f in ("status", "depth_final", "hwm_bytes", "spill_bytes", "chk"):
+        assert np.array_equal(gs[f], rs[f]), f
+    stats = dsr.dsr_serve_stats(rt.ctx)
+    assert stats["submitted"] == stats["completed"] == 400 and stats["errors"] == 0
+
+
+def test_serve_open_loop_latencies(rt):
+    import paper_1711_10413_gb300 as dsr
+    work = wl.hetero(n_instances=3000, max_teams=64)
+    b = rt.serve_start(work, threads=128, slab_bytes=16384, capacity=1024)
+    try:
+        arr = wl.poisson_arrivals(3000, 100000.0)
+        lat, el = dsr.dsr_serve_bench(rt.ctx, b["descs"], arr)
+    finally:
+        rt.serve_stop()
+    assert (lat > 0).all() and el > 0
+    r, _ = oracle.run_workload(work, slab_bytes=16384, overflow_bytes=3 * 32768)
+    assert np.array_equal(b["out"].cpu().numpy(), r)
+
+
+def test_serve_small_ring_admission(rt):
+    import paper_1711_10413_gb300 as dsr
+    work = wl.hetero(n_instances=120, max_teams=6)
+    b = rt.serve_start(work, threads=128, slab_bytes=4096, capacity=4)
+    try:
+        budget_hits = 0
+        tickets, pending = [], list(work.regions)
+        t0 = time.time()
+        while pending:
+            assert time.time() - t0 < 30
+            tk = dsr.dsr_serve_submit(rt.ctx, pending[0])
+            if tk is None:
+                budget_hits += 1
+                dsr.dsr_serve_poll(rt.ctx, 1 << 62)
+                continue
+            tickets.append(tk)
+            pending.pop(0)
+        _wait_all(dsr, rt, tickets)
+    finally:
+        rt.serve_stop()
+    assert budget_hits > 0
+    r, _ = oracle.run_workload(work, slab_bytes=4096, overflow_bytes=3 * 32768)
+    assert np.array_equal(b["out"].cpu().numpy(), r)
+
+
+def test_serve_idle_exit_and_restart(rt):
+    import paper_1711_10413_gb300 as dsr
+    work = wl.hetero(n_instances=40, max_teams=4)
+    b = rt.serve_start(work, threads=128, slab_bytes=16384, capacity=64,
+                       idle_timeout_ns=50_000_000)
+    try:
+        t1 = _submit_all(dsr, rt, work.regions[:20])
+        _wait_all(dsr, rt, t1)
+        time.sleep(0.5)   # every server CTA leaves after 50 ms without work
+        assert dsr.dsr_serve_stats(rt.ctx)["idle_exits"] > 0
+        t2 = _submit_all(dsr, rt, work.regions[20:])
+        _wait_all(dsr, rt, t2)
+    finally:
+        rt.serve_stop()
+    r, _ = oracle.run_workload(work, slab_bytes=16384, overflow_bytes=3 * 32768)
+    assert np.array_equal(b["out"].cpu().numpy(), r)
+
+
+def test_serve_nested_program(rt):
+    import paper_1711_10413_gb300 as dsr
+    work = wl.nested(teams=512, threads=256, depth=3)
+    b = rt.serve_start(work, threads=256, slab_bytes=4096, capacity=8)
+    try:
+        st = _wait_all(dsr, rt, _submit_all(dsr, rt, work.regions))
+    finally:
+        rt.serve_stop()
+    assert list(st.values()) == [0]
+    r, rs = oracle.run_workload(work, slab_bytes=4096)
+    assert np.array_equal(b["out"].cpu().numpy(), r)
+
+
+def test_serve_rejects_bad_requests_on_the_host(rt):
+    import paper_1711_10413_gb300 as dsr
+    work = wl.hetero(n_instances=10, max_teams=4)
+    rt.serve_start(work, threads=128, slab_bytes=4096, capacity=16)
+    try:
+        bad = dict(work.regions[0].as_dict(), out_offset=1 << 40)
+        with pytest.raises(dsr.DsrError) as ei:
+            dsr.dsr_serve_submit(rt.ctx, bad)
+        assert ei.value.code == dsr.DSR_ERR_INVALID
+        other = dict(work.regions[0].as_dict(), program=dsr.DSR_PROG_NESTED)
+        with pytest.raises(dsr.DsrError):
+            dsr.dsr_serve_submit(rt.ctx, other)
+    finally:
+        rt.serve_stop()

@@ -305,9 +305,12 @@ static int32_t set_batch_attrs(dsr_ctx *ctx) {
   if (b->attrs_set) return DSR_OK;
   for (uint32_t p = DSR_PROG_PAPER_SCALARS; p <= DSR_PROG_HETERO; ++p)
     for (uint32_t t : {128u, 256u, 1024u}) {
-      cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(batch_kernel_for(p, t)),
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+      const void *k = reinterpret_cast<const void *>(batch_kernel_for(p, t));
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            ctx->max_smem_optin);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
       if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "cudaFuncSetAttribute (batch)");
     }
   b->attrs_set = true;

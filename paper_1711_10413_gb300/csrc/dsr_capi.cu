@@ -247,9 +247,12 @@ static int32_t set_smem_attr(dsr_ctx *ctx, uint32_t smem) {
   static const uint32_t kThreads[] = {128, 256, 512, 1024};
   for (uint32_t p = DSR_PROG_PAPER_SCALARS; p <= DSR_PROG_HETERO; ++p)
     for (uint32_t t : kThreads) {
-      cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(plain_kernel_for(p, t)),
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+      const void *k = reinterpret_cast<const void *>(plain_kernel_for(p, t));
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(smem));
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
       if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "cudaFuncSetAttribute");
     }
   return DSR_OK;

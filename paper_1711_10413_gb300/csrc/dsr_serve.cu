@@ -173,10 +173,11 @@ __global__ void __launch_bounds__(MAXT, MINB) serve_kernel(const __grid_constant
     return;
   }
   const uint32_t lane = lane_id();
-  if (blockIdx.x == gridDim.x - 1) {
-    // The doorbell: the only reader of host memory. It copies the host's
-    // tail (and stop flag) into device memory, where the other CTAs poll,
-    // and leaves on stop or after idle_timeout_ns without a new request.
+  if (blockIdx.x == 0) {
+    // The doorbell (block 0, the first to be scheduled): the main reader of
+    // host memory. It copies the host's tail (and stop flag) into device
+    // memory, where the other CTAs poll, and leaves on stop or after
+    // idle_timeout_ns without a new request.
     if (lane == 0) {
       unsigned long long last = ld_relaxed_gpu(&a.ws->tail);
       uint64_t idle_since = globaltimer();
@@ -184,12 +185,12 @@ __global__ void __launch_bounds__(MAXT, MINB) serve_kernel(const __grid_constant
         const unsigned long long stop = ld_acquire_sys(&a.hs->stop);
         const unsigned long long t = ld_acquire_sys(&a.hs->tail);
         if (t != last) {
-          st_release_gpu(&a.ws->tail, t);
+          atomicMax(&a.ws->tail, t);
           last = t;
           idle_since = globaltimer();
         }
         if (stop) {
-          st_release_gpu(&a.ws->stop, 1ull);
+          atomicExch(&a.ws->stop, 1ull);
           break;
         }
         if (globaltimer() - idle_since > a.idle_timeout_ns) {
@@ -216,7 +217,16 @@ __global__ void __launch_bounds__(MAXT, MINB) serve_kernel(const __grid_constant
       // nothing to run: leave when asked to stop (all submitted work has
       // been claimed) or after the idle timeout; otherwise back off
       unsigned long long stop = 0;
-      if (lane == 0) stop = ld_acquire_gpu(&a.ws->stop);
+      if (lane == 0) {
+        stop = ld_acquire_gpu(&a.ws->stop);
+        // a few CTAs also look at host memory now and then, so the server
+        // does not depend on the doorbell alone being resident
+        if (!stop && (blockIdx.x & 63u) == 1u && backoff >= 4096) {
+          const unsigned long long t = ld_acquire_sys(&a.hs->tail);
+          if (t > ld_relaxed_gpu(&a.ws->tail)) atomicMax(&a.ws->tail, t);
+          if (ld_acquire_sys(&a.hs->stop)) atomicExch(&a.ws->stop, 1ull);
+        }
+      }
       stop = __shfl_sync(0xffffffffu, stop, 0);
       if (stop) break;
       if (globaltimer() - idle_since > a.idle_timeout_ns) {
@@ -482,7 +492,10 @@ extern "C" int32_t dsr_serve_start(dsr_ctx *ctx, const dsr_serve_cfg *cfg, void 
   ServeFn k = serve_kernel_for(cfg->program, cfg->threads);
   if ((e = cudaFuncSetAttribute(reinterpret_cast<const void *>(k),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                ctx->max_smem_optin)) != cudaSuccess) {
+                                ctx->max_smem_optin)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(reinterpret_cast<const void *>(k),
+                                cudaFuncAttributePreferredSharedMemoryCarveout,
+                                cudaSharedmemCarveoutMaxShared)) != cudaSuccess) {
     int32_t rc = dsr_cuda_fail(ctx, e, "serve attributes");
     dsr_serve_release(ctx);
     return rc;

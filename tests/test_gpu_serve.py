@@ -122,7 +122,8 @@ def test_serve_idle_exit_and_restart(rt):
         t1 = _submit_all(dsr, rt, work.regions[:20])
         _wait_all(dsr, rt, t1)
         time.sleep(0.5)   # every server CTA leaves after 50 ms without work
-        assert dsr.dsr_serve_stats(rt.ctx)["idle_exits"] > 0
+        stats = dsr.dsr_serve_stats(rt.ctx)
+        assert stats["idle_exits"] > 0, stats
         t2 = _submit_all(dsr, rt, work.regions[20:])
         _wait_all(dsr, rt, t2)
     finally:

@@ -274,6 +274,32 @@ int32_t dsr_launch_regions(dsr_ctx *ctx, const dsr_region_desc *descs_host, uint
                            uint64_t out_bytes, dsr_team_status *status_dev, uint64_t n_status,
                            void *stream);
 
+/* Batched launch that allocates nothing. The paper has no counterpart: it
+ * is here for callers that cannot allocate device memory -- code on a path
+ * where cudaMalloc/cudaFree are not allowed (they can synchronise the
+ * whole device), or a plug-in whose host application owns all device
+ * memory through its own allocator. The same run as dsr_launch_batch
+ * (same arguments but no workspace and no graph flag), with its workspace
+ * in a file-scope device array of dsr_batch_static_capacity() bytes (8 MiB:
+ * about one million teams) that every GPU loading this library keeps until
+ * the process exits. A batch whose workspace would be larger is refused
+ * with DSR_ERR_BUDGET. The first call on a device finds the array's device
+ * address (cudaGetSymbolAddress, with that device made current for the
+ * call) and sets the kernels' shared-memory limit; make that first call
+ * before any stream capture. All calls share the one array and leave its
+ * contents behind (each call re-initialises what it reads), so calls whose
+ * launches overlap on the GPU -- on different streams without ordering, or
+ * from different threads -- race and must not be issued. Overflow slabs
+ * still come from the ctx's pool when dsr_stack_init configured one. */
+int32_t dsr_launch_batch_static(dsr_ctx *ctx, const dsr_region_desc *descs_dev, uint32_t n,
+                                uint32_t program, uint64_t total_teams, const void *images_dev,
+                                uint64_t image_bytes, void *out_dev, uint64_t out_bytes,
+                                dsr_team_status *status_dev, uint64_t n_status,
+                                const dsr_batch_tuning *tuning, void *stream);
+
+/* Size in bytes of the fixed workspace dsr_launch_batch_static uses. */
+uint64_t dsr_batch_static_capacity(void);
+
 /* ---- served form: a device-resident request loop ------------------------ */
 
 /* A server: one persistent kernel that keeps every CTA's stack live and runs

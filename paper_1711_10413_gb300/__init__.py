@@ -112,6 +112,9 @@ def _declare(L):
         "dsr_autotune": (_i32, [_vp, _vp, _u32, _u32, _u64, _vp, _u64, _vp, _u64, _vp, _u64, _vp,
                                 _u64, _vp, P(dsr_batch_tuning), P(ctypes.c_float)]),
         "dsr_launch_regions": (_i32, [_vp, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u64, _vp]),
+        "dsr_launch_batch_static": (_i32, [_vp, _vp, _u32, _u32, _u64, _vp, _u64, _vp, _u64,
+                                           _vp, _u64, P(dsr_batch_tuning), _vp]),
+        "dsr_batch_static_capacity": (_u64, []),
         "dsr_serve_workspace_bytes": (_u64, [_u32]),
         "dsr_serve_start": (_i32, [_vp, P(dsr_serve_cfg), _vp, _u64]),
         "dsr_serve_submit": (_i32, [_vp, P(dsr_region_desc), P(_u64)]),
@@ -149,7 +152,8 @@ def exported_symbols():
             "dsr_validate_region", "dsr_region_extent", "dsr_footprint_model",
             "dsr_launch_region", "dsr_run_region_host", "dsr_batch_workspace_bytes",
             "dsr_batch_count", "dsr_launch_batch", "dsr_batch_errors", "dsr_autotune",
-            "dsr_launch_regions", "dsr_serve_workspace_bytes", "dsr_serve_start",
+            "dsr_launch_regions", "dsr_launch_batch_static", "dsr_batch_static_capacity",
+            "dsr_serve_workspace_bytes", "dsr_serve_start",
             "dsr_serve_submit", "dsr_serve_poll", "dsr_serve_stop", "dsr_serve_stats",
             "dsr_serve_bench", "dsr_launch_bench"]
 
@@ -309,6 +313,22 @@ def dsr_launch_batch(ctx: int, descs_dev, n: int, program: int, total_teams: int
                                   _nbytes(out), _ptr(status), _nbytes(status) // 32,
                                   _ptr(workspace), _nbytes(workspace), _tuning(tuning),
                                   _stream(stream), 1 if use_graph else 0), ctx)
+
+
+def dsr_launch_batch_static(ctx: int, descs_dev, n: int, program: int, total_teams: int,
+                            images, out, status, tuning=None, stream=None):
+    """The batched launch with its workspace in the library's fixed device
+    array (no workspace argument, nothing allocated)."""
+    _check(lib().dsr_launch_batch_static(ctx, _ptr(descs_dev), n, program, total_teams,
+                                         _ptr(images),
+                                         _nbytes(images) if images is not None else 0,
+                                         _ptr(out), _nbytes(out), _ptr(status),
+                                         _nbytes(status) // 32, _tuning(tuning),
+                                         _stream(stream)), ctx)
+
+
+def dsr_batch_static_capacity() -> int:
+    return int(lib().dsr_batch_static_capacity())
 
 
 def dsr_batch_errors(ctx: int, workspace, stream=None):

@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "dsr.h"
@@ -573,4 +574,89 @@ extern "C" int32_t dsr_launch_regions(dsr_ctx *ctx, const dsr_region_desc *descs
     if (rc != DSR_OK) return rc;
   }
   return DSR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched launch without allocation
+//
+// For callers that cannot allocate device memory -- code that must not call
+// cudaMalloc/cudaFree (they can synchronise the device), or a host whose
+// device memory is owned by another allocator -- the batch workspace can
+// live in this fixed file-scope array instead of a caller buffer. Every GPU
+// that loads this library keeps the array for the life of the process.
+// ---------------------------------------------------------------------------
+static constexpr uint64_t kStaticWsBytes = 8ull << 20;  // 8 MiB
+static __device__ __align__(256) uint8_t g_static_ws[kStaticWsBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void *g_static_ptr[kMaxDevices];      // device address of g_static_ws, per device
+bool g_static_attrs[kMaxDevices];     // batch kernels' shared-memory limit set
+
+// Once per device, with that device current: the array's device address
+// (the host-side symbol is only a stand-in for it) and the batch kernels'
+// dynamic shared-memory limit.
+int32_t static_setup(dsr_ctx *ctx, void **ws) {
+  if (ctx->device < 0 || ctx->device >= kMaxDevices)
+    return dsr_fail(ctx, DSR_ERR_INVALID, "device ordinal out of range");
+  std::lock_guard<std::mutex> g(g_static_mu);
+  if (!g_static_ptr[ctx->device] || !g_static_attrs[ctx->device]) {
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "cudaGetDevice");
+    if (cur != ctx->device && (e = cudaSetDevice(ctx->device)) != cudaSuccess)
+      return dsr_cuda_fail(ctx, e, "cudaSetDevice");
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_ws);
+    if (e == cudaSuccess)
+      for (uint32_t prog = DSR_PROG_PAPER_SCALARS; prog <= DSR_PROG_HETERO && e == cudaSuccess; ++prog)
+        for (uint32_t t : {128u, 256u, 1024u}) {
+          const void *k = reinterpret_cast<const void *>(batch_kernel_for(prog, t));
+          e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   ctx->max_smem_optin);
+          if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
+          if (e != cudaSuccess) break;
+        }
+    if (cur != ctx->device) cudaSetDevice(cur);
+    if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "static workspace set-up");
+    g_static_ptr[ctx->device] = p;
+    g_static_attrs[ctx->device] = true;
+  }
+  *ws = g_static_ptr[ctx->device];
+  return DSR_OK;
+}
+}  // namespace
+
+extern "C" uint64_t dsr_batch_static_capacity(void) { return kStaticWsBytes; }
+
+extern "C" int32_t dsr_launch_batch_static(dsr_ctx *ctx, const dsr_region_desc *descs_dev,
+                                           uint32_t n, uint32_t program, uint64_t total_teams,
+                                           const void *images_dev, uint64_t image_bytes,
+                                           void *out_dev, uint64_t out_bytes,
+                                           dsr_team_status *status_dev, uint64_t n_status,
+                                           const dsr_batch_tuning *tuning, void *stream) {
+  if (!ctx) return dsr_fail(nullptr, DSR_ERR_INVALID, "null ctx");
+  if (!ctx->stack_ready) return dsr_fail(ctx, DSR_ERR_INVALID, "dsr_stack_init not called");
+  if (!descs_dev || n == 0 || !out_dev || !status_dev)
+    return dsr_fail(ctx, DSR_ERR_INVALID, "null batch argument or empty batch");
+  if (reinterpret_cast<uintptr_t>(descs_dev) & 15u)
+    return dsr_fail(ctx, DSR_ERR_INVALID, "descriptors must be 16-byte aligned");
+  if (total_teams >= 0xffffffffull || ws_bytes(n, total_teams) > kStaticWsBytes)
+    return dsr_fail(ctx, DSR_ERR_BUDGET,
+                    "a batch of %llu teams needs %llu workspace bytes; the static workspace "
+                    "holds %llu (use dsr_launch_batch with a caller buffer)",
+                    (unsigned long long)total_teams,
+                    (unsigned long long)ws_bytes(n, total_teams),
+                    (unsigned long long)kStaticWsBytes);
+  void *ws = nullptr;
+  int32_t rc = static_setup(ctx, &ws);
+  if (rc != DSR_OK) return rc;
+  BatchCall c{descs_dev, n, program, total_teams, images_dev, image_bytes, out_dev,
+              out_bytes, status_dev, n_status, ws, kStaticWsBytes};
+  uint32_t threads, slab, grid;
+  if ((rc = resolve_tuning(ctx, c, tuning, &threads, &slab, &grid)) != DSR_OK) return rc;
+  return enqueue_batch(ctx, c, threads, slab, grid, static_cast<cudaStream_t>(stream));
 }

@@ -6,6 +6,18 @@ threads, 3 nested levels each pushing a 1088-byte frame (16 int32 scalars
 + int32[256]), 4M int32 output -- one region instance per step, launched
 through the C ABI. Metric: regions/s, with push+pop/s beside it.
 
+The same JSON line also carries the other launch forms, each on its own
+configuration (`--forms none` skips them):
+  scalars  - 1 team x 128 threads, 1000 sequential regions: one launch that
+             runs them all against 1000 launches of one region each;
+  batched  - 10,000 heterogeneous instances (log-uniform teams and frame
+             sizes) in one persistent launch replayed from a CUDA graph,
+             against one plain launch per instance;
+  served   - the same instance distribution submitted open-loop (Poisson)
+             to the device-resident server at several rates: p50/p99
+             latency and sustained requests/s, against one plain launch per
+             request under the same arrivals.
+
 Prints ONE JSON line (rank 0). `--impl reference` times the CPU oracle on
 the same workload instead.
 """
@@ -133,6 +145,93 @@ def time_oracle(work, slab, ovf, budget_s: float = 10.0):
 
 
 # ---------------------------------------------------------------------------
+# The other launch forms
+# ---------------------------------------------------------------------------
+def _event_ms(torch, fn, reps, flush=None):
+    s = torch.cuda.current_stream()
+    fn()
+    torch.cuda.synchronize()
+    out = []
+    for i in range(reps):
+        if flush is not None:
+            flush.fill_(i)
+        a = torch.cuda.Event(enable_timing=True)
+        z = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn()
+        z.record(s)
+        torch.cuda.synchronize()
+        out.append(a.elapsed_time(z))
+    return float(np.median(out))
+
+
+def measure_forms(dsr, torch, device, flush):
+    forms = {}
+    rt = dsr.Runtime(device, slab_bytes=16384, overflow_bytes_per_team=3 * 32768, max_teams=4096)
+    # config 1: 1000 sequential regions of one team
+    sc = wl.scalars(n_regions=1000, teams=1, threads=128)
+    one = wl.scalars(n_regions=1, teams=1, threads=128)
+    rt.configure(1024, 3 * 32768, 4096)
+    images, out, status = rt.device_buffers(sc)
+    r_all = sc.regions[0]
+    ms_all = _event_ms(torch, lambda: dsr.dsr_launch_region(rt.ctx, r_all, images, out, status),
+                       10, flush)
+    descs = dsr.pack_descs([dict(one.regions[0].as_dict(), image_offset=16 * i,
+                                 out_offset=4 * 96 * i) for i in range(1000)])
+    ms_each = _event_ms(torch, lambda: dsr.dsr_launch_regions(rt.ctx, descs, images, out, status),
+                        3, flush)
+    forms["scalars"] = dict(workload="scalars_1x128_r1000", regions=1000,
+                            one_launch_regions_per_s=1000 / (ms_all * 1e-3),
+                            per_launch_regions_per_s=1000 / (ms_each * 1e-3),
+                            handoff_ns_per_region=ms_all * 1e6 / 1000)
+    # config 4: batched vs per-launch
+    rt.configure(16384, 3 * 32768, 4096)
+    work = wl.hetero(n_instances=10000)
+    b = rt.batch_buffers(work)
+    tuning, _ = rt.autotune(b)
+    ms_batch = _event_ms(torch, lambda: rt.launch_batch(b, tuning, use_graph=True), 5, flush)
+    err, counted = rt.batch_errors(b)
+    ms_plain = _event_ms(torch, lambda: rt.launch_regions(b), 2, flush)
+    st = b["status"].cpu().numpy().view(dsr.TEAM_STATUS_DTYPE)
+    forms["batched"] = dict(workload="hetero_10000_instances", instances=10000, teams=counted,
+                            tuning=tuning, batched_regions_per_s=10000 / (ms_batch * 1e-3),
+                            per_launch_regions_per_s=10000 / (ms_plain * 1e-3),
+                            batched_push_pop_per_s=sum(r.teams * r.depth for r in work.regions)
+                            / (ms_batch * 1e-3),
+                            speedup=ms_plain / ms_batch, device_rejects=err,
+                            bad_team_status=int((st["status"] != 0).sum()))
+    del b
+    # config 5: served at several rates vs per-request launches
+    n = 20000
+    sw = wl.hetero(n_instances=n)
+    bs = rt.serve_start(sw, threads=tuning["threads"], slab_bytes=tuning["slab_bytes"],
+                        capacity=8192)
+    served = {}
+    try:
+        for rate in (50000, 100000, 200000, 500000):
+            lat, el = dsr.dsr_serve_bench(rt.ctx, bs["descs"], wl.poisson_arrivals(n, float(rate)))
+            ok = lat[lat >= 0]
+            served[str(rate)] = dict(p50_us=float(np.percentile(ok, 50)) / 1e3,
+                                     p99_us=float(np.percentile(ok, 99)) / 1e3,
+                                     sustained_regions_per_s=n / (el * 1e-9),
+                                     failed=int((lat < 0).sum()))
+    finally:
+        rt.serve_stop()
+    launched = {}
+    for rate in (50000, 100000):
+        m = 5000
+        lat, el = dsr.dsr_launch_bench(rt.ctx, bs["descs"][:m], wl.poisson_arrivals(m, float(rate)),
+                                       bs["images"], bs["out"], bs["status"])
+        launched[str(rate)] = dict(p50_us=float(np.percentile(lat, 50)) / 1e3,
+                                   p99_us=float(np.percentile(lat, 99)) / 1e3,
+                                   sustained_regions_per_s=m / (el * 1e-9))
+    forms["served"] = dict(workload="hetero_poisson_%d_requests" % n, overflow_pool_bytes=
+                           3 * 32768 * 4096, server=served, per_request_launch=launched)
+    rt.close()
+    return forms
+
+
+# ---------------------------------------------------------------------------
 # Main
 # ---------------------------------------------------------------------------
 def main():
@@ -144,6 +243,7 @@ def main():
     ap.add_argument("--workload", default="nested")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--forms", default="all", choices=["all", "none"])
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -282,6 +382,8 @@ def main():
         bad_team_status=bad_status,
         clocks=clk,
     )
+    if world == 1 and args.forms == "all":
+        line["forms"] = measure_forms(dsr, torch, local, flush)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = time_oracle(work, slab, ovf, budget_s=args.cpu_budget)
     print(json.dumps(line))

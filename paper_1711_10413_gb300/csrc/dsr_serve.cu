@@ -23,9 +23,13 @@
 // 64-bit atomic add on the claim word and keeps it only when the sequence
 // half still names the request it read, so a slot reused for a later
 // request is never mistaken for an earlier one.
-// Only one CTA, the doorbell, reads host memory: it copies the tail and the
-// stop flag into device memory, where the other CTAs poll with backoff, so
-// idle CTAs do not flood the host memory with reads.
+// One CTA, the doorbell, reads host memory: it copies every new request's
+// descriptor into a device-memory ring and then the tail and the stop flag
+// into device memory, where the other CTAs poll with backoff; the other CTAs
+// never read host memory (a few do, rarely, when idle, so the server does
+// not depend on the doorbell being resident). CTAs claim teams from a window
+// of the oldest requests in flight, starting at different requests, so the
+// claims do not all contend on one word.
 // Every device-side wait is bounded: a CTA that finds no work for
 // idle_timeout_ns leaves (the host restarts the server on the next submit
 // or poll).
@@ -78,7 +82,8 @@ struct ServeWs {  // device workspace header
 };
 
 struct ServeArgs {
-  const dsr_region_desc *ring;  // device view of the submit ring
+  const dsr_region_desc *ring;  // device view of the submit ring (host memory)
+  dsr_region_desc *dring;       // device copy of the submit ring
   HostShared *hs;               // device view
   CompRec *comp;                // device view of the completion ring
   ServeWs *ws;
@@ -124,35 +129,42 @@ __device__ __forceinline__ void st_release_gpu(unsigned long long *p, unsigned l
 }
 
 // Claim one team of a submitted request (master warp). Returns false when
-// no team is available now.
+// no team is available now. The CTA looks at the kWindow oldest requests in
+// flight, starting at one that depends on its block index.
+constexpr uint32_t kWindow = 32;
+
 __device__ __forceinline__ bool claim(const ServeArgs &a, unsigned long long *seq,
                                       uint32_t *team) {
   unsigned long long out_seq = 0;
   uint32_t out_team = 0, got = 0;
   if (lane_id() == 0) {
-    for (int tries = 0; tries < 64 && !got; ++tries) {
+    for (int tries = 0; tries < 8 && !got; ++tries) {
       const unsigned long long h = ld_relaxed_gpu(&a.ws->head);
       const unsigned long long tail = ld_acquire_gpu(&a.ws->tail);
       if (h >= tail) break;
-      const uint32_t slot = static_cast<uint32_t>(h % a.capacity);
-      const uint32_t T = a.ring[slot].teams;
-      unsigned long long w = ld_relaxed_gpu(&a.slots[slot].claim);
-      bool advance = false;
-      for (int cas = 0; cas < 32; ++cas) {
-        if ((w >> 32) != (h & 0xffffffffull) || static_cast<uint32_t>(w) >= T) {
-          advance = true;  // h's teams are all handed out, or h is done
-          break;
+      const uint32_t n = static_cast<uint32_t>(min(tail - h, static_cast<unsigned long long>(kWindow)));
+      const uint32_t start = (blockIdx.x * 7u + static_cast<uint32_t>(tries)) % n;
+      for (uint32_t j = 0; j < n && !got; ++j) {
+        const unsigned long long r = h + (start + j) % n;
+        const uint32_t slot = static_cast<uint32_t>(r % a.capacity);
+        const uint32_t T = a.dring[slot].teams;
+        unsigned long long w = ld_relaxed_gpu(&a.slots[slot].claim);
+        for (int cas = 0; cas < 4; ++cas) {
+          if ((w >> 32) != (r & 0xffffffffull) || static_cast<uint32_t>(w) >= T) {
+            // r's teams are all handed out (or r is done): the head may pass it
+            if (r == h) atomicCAS(&a.ws->head, h, h + 1);
+            break;
+          }
+          const unsigned long long prev = atomicCAS(&a.slots[slot].claim, w, w + 1);
+          if (prev == w) {
+            got = 1;
+            out_seq = r;
+            out_team = static_cast<uint32_t>(w);
+            break;
+          }
+          w = prev;
         }
-        const unsigned long long prev = atomicCAS(&a.slots[slot].claim, w, w + 1);
-        if (prev == w) {
-          got = 1;
-          out_seq = h;
-          out_team = static_cast<uint32_t>(w);
-          break;
-        }
-        w = prev;
       }
-      if (advance) atomicCAS(&a.ws->head, h, h + 1);
     }
   }
   got = __shfl_sync(0xffffffffu, got, 0);
@@ -175,30 +187,41 @@ __global__ void __launch_bounds__(MAXT, MINB) serve_kernel(const __grid_constant
   const uint32_t lane = lane_id();
   if (blockIdx.x == 0) {
     // The doorbell (block 0, the first to be scheduled): the main reader of
-    // host memory. It copies the host's tail (and stop flag) into device
-    // memory, where the other CTAs poll, and leaves on stop or after
-    // idle_timeout_ns without a new request.
-    if (lane == 0) {
-      unsigned long long last = ld_relaxed_gpu(&a.ws->tail);
-      uint64_t idle_since = globaltimer();
-      for (;;) {
-        const unsigned long long stop = ld_acquire_sys(&a.hs->stop);
-        const unsigned long long t = ld_acquire_sys(&a.hs->tail);
-        if (t != last) {
-          atomicMax(&a.ws->tail, t);
-          last = t;
-          idle_since = globaltimer();
-        }
-        if (stop) {
-          atomicExch(&a.ws->stop, 1ull);
-          break;
-        }
-        if (globaltimer() - idle_since > a.idle_timeout_ns) {
-          atomicAdd(&a.ws->idle_exits, 1u);
-          break;
-        }
-        __nanosleep(256);
+    // host memory. For every new request it copies the descriptor into the
+    // device ring (the warp's lanes copy 16 bytes each), then publishes the
+    // new tail (and a stop) in device memory, where the other CTAs poll. It
+    // leaves on stop or after idle_timeout_ns without a new request.
+    unsigned long long last = ld_relaxed_gpu(&a.ws->tail);
+    uint64_t idle_since = globaltimer();
+    for (;;) {
+      unsigned long long stop = 0, t = 0;
+      if (lane == 0) {
+        stop = ld_acquire_sys(&a.hs->stop);
+        t = ld_acquire_sys(&a.hs->tail);
       }
+      stop = __shfl_sync(0xffffffffu, stop, 0);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      if (t > last) {
+        for (unsigned long long r = last + lane / 4u; r < t; r += 8u) {
+          const uint32_t slot = static_cast<uint32_t>(r % a.capacity);
+          reinterpret_cast<uint4 *>(a.dring + slot)[lane & 3u] =
+              reinterpret_cast<const uint4 *>(a.ring + slot)[lane & 3u];
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) atomicMax(&a.ws->tail, t);
+        last = t;
+        idle_since = globaltimer();
+      }
+      if (stop) {
+        if (lane == 0) atomicExch(&a.ws->stop, 1ull);
+        break;
+      }
+      if (globaltimer() - idle_since > a.idle_timeout_ns) {
+        if (lane == 0) atomicAdd(&a.ws->idle_exits, 1u);
+        break;
+      }
+      __nanosleep(256);
     }
     __syncwarp();
     terminate_workers();
@@ -219,13 +242,11 @@ __global__ void __launch_bounds__(MAXT, MINB) serve_kernel(const __grid_constant
       unsigned long long stop = 0;
       if (lane == 0) {
         stop = ld_acquire_gpu(&a.ws->stop);
-        // a few CTAs also look at host memory now and then, so the server
-        // does not depend on the doorbell alone being resident
-        if (!stop && (blockIdx.x & 63u) == 1u && backoff >= 4096) {
-          const unsigned long long t = ld_acquire_sys(&a.hs->tail);
-          if (t > ld_relaxed_gpu(&a.ws->tail)) atomicMax(&a.ws->tail, t);
-          if (ld_acquire_sys(&a.hs->stop)) atomicExch(&a.ws->stop, 1ull);
-        }
+        // a few CTAs also look at the host's stop flag now and then, so a
+        // stop is seen even when the doorbell has left
+        if (!stop && (blockIdx.x & 63u) == 1u && backoff >= 4096 &&
+            ld_acquire_sys(&a.hs->stop))
+          atomicExch(&a.ws->stop, 1ull);
       }
       stop = __shfl_sync(0xffffffffu, stop, 0);
       if (stop) break;
@@ -243,7 +264,7 @@ __global__ void __launch_bounds__(MAXT, MINB) serve_kernel(const __grid_constant
     __syncwarp();
     if (lane < 4)
       reinterpret_cast<uint4 *>(&c->desc)[lane] =
-          reinterpret_cast<const uint4 *>(a.ring + slot)[lane];
+          reinterpret_cast<const uint4 *>(a.dring + slot)[lane];
     if (lane == 0) c->team = team;
     __syncwarp();
     e.d = &c->desc;
@@ -313,7 +334,8 @@ ServeFn serve_kernel_for(uint32_t program, uint32_t threads) {
 }
 
 uint64_t serve_ws_bytes(uint32_t capacity) {
-  return sizeof(ServeWs) + sizeof(SlotState) * static_cast<uint64_t>(capacity);
+  return sizeof(ServeWs) + (sizeof(SlotState) + sizeof(dsr_region_desc)) *
+                               static_cast<uint64_t>(capacity);
 }
 
 __global__ void serve_init(ServeWs *ws, SlotState *slots, uint32_t capacity) {
@@ -358,6 +380,7 @@ struct dsr_serve_state {
   // device workspace (caller-owned)
   ServeWs *ws = nullptr;
   SlotState *slots = nullptr;
+  dsr_region_desc *dring = nullptr;
   // host bookkeeping
   uint64_t next_seq = 0;       // next ticket
   uint64_t comp_pos = 0;       // next completion record to read
@@ -367,6 +390,7 @@ struct dsr_serve_state {
   std::unordered_map<uint64_t, uint64_t> reserved;  // ticket -> overflow bytes reserved
   uint64_t reserved_bytes = 0;
   uint64_t pool_budget = 0;
+  uint64_t next_alive_check = 0;  // host time of the next server-exit check
 };
 
 void dsr_serve_release(dsr_ctx *ctx) {
@@ -383,11 +407,28 @@ void dsr_serve_release(dsr_ctx *ctx) {
 
 namespace {
 
+inline uint64_t now_ns() {
+  return static_cast<uint64_t>(std::chrono::duration_cast<std::chrono::nanoseconds>(
+                                   std::chrono::steady_clock::now().time_since_epoch())
+                                   .count());
+}
+
+// Has the server kernel left (idle timeout)? Asked of the driver at most
+// once per millisecond: the query costs microseconds.
+bool server_exited(dsr_serve_state *sv) {
+  if (!sv->running) return true;
+  const uint64_t t = now_ns();
+  if (t < sv->next_alive_check) return false;
+  sv->next_alive_check = t + 1000000;
+  return cudaStreamQuery(sv->stream) == cudaSuccess;
+}
+
 int32_t launch_server(dsr_ctx *ctx, dsr_serve_state *sv) {
   if (sv->launched) serve_reopen<<<1, 1, 0, sv->stream>>>(sv->ws);
   sv->launched = true;
   ServeArgs a;
   a.ring = sv->ring_dev;
+  a.dring = sv->dring;
   a.hs = sv->hs_dev;
   a.comp = sv->comp_dev;
   a.ws = sv->ws;
@@ -489,6 +530,7 @@ extern "C" int32_t dsr_serve_start(dsr_ctx *ctx, const dsr_serve_cfg *cfg, void 
   sv->slot_busy.assign(cfg->capacity, 0);
   sv->ws = static_cast<ServeWs *>(workspace_dev);
   sv->slots = reinterpret_cast<SlotState *>(static_cast<uint8_t *>(workspace_dev) + sizeof(ServeWs));
+  sv->dring = reinterpret_cast<dsr_region_desc *>(sv->slots + cfg->capacity);
   ServeFn k = serve_kernel_for(cfg->program, cfg->threads);
   if ((e = cudaFuncSetAttribute(reinterpret_cast<const void *>(k),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -541,7 +583,7 @@ extern "C" int32_t dsr_serve_submit(dsr_ctx *ctx, const dsr_region_desc *d, uint
   if (sv->reserved_bytes + want > sv->pool_budget)
     return dsr_fail(ctx, DSR_ERR_BUDGET, "overflow pool budget in use");
   // a server that left after its idle timeout is started again
-  if (sv->running && cudaStreamQuery(sv->stream) == cudaSuccess) sv->running = false;
+  if (sv->running && server_exited(sv)) sv->running = false;
   if (!sv->running && (rc = launch_server(ctx, sv)) != DSR_OK) return rc;
   const uint64_t seq = sv->next_seq++;
   sv->ring[seq % sv->cfg.capacity] = *d;
@@ -559,7 +601,7 @@ extern "C" int32_t dsr_serve_poll(dsr_ctx *ctx, uint64_t ticket, int32_t *status
   if (!ctx || !ctx->serve || !status) return dsr_fail(ctx, DSR_ERR_INVALID, "not serving");
   dsr_serve_state *sv = ctx->serve;
   drain_completions(sv);
-  if (sv->running && sv->completed < sv->next_seq && cudaStreamQuery(sv->stream) == cudaSuccess) {
+  if (sv->running && sv->completed < sv->next_seq && server_exited(sv)) {
     // every CTA left after the idle timeout while work was published
     sv->running = false;
     int32_t rc = launch_server(ctx, sv);
@@ -605,14 +647,6 @@ extern "C" int32_t dsr_serve_stats(dsr_ctx *ctx, uint64_t *submitted, uint64_t *
 // ---------------------------------------------------------------------------
 // Open-loop latency harnesses (host threads; the clock is CLOCK_MONOTONIC)
 // ---------------------------------------------------------------------------
-namespace {
-inline uint64_t now_ns() {
-  return static_cast<uint64_t>(std::chrono::duration_cast<std::chrono::nanoseconds>(
-                                   std::chrono::steady_clock::now().time_since_epoch())
-                                   .count());
-}
-}  // namespace
-
 extern "C" int32_t dsr_serve_bench(dsr_ctx *ctx, const dsr_region_desc *descs, uint32_t n,
                                    const int64_t *arrival_ns, int64_t *latency_ns,
                                    int64_t *elapsed_ns) {

@@ -254,7 +254,7 @@ int32_t dsr_batch_errors(dsr_ctx *ctx, const void *workspace_dev, uint32_t *erro
                          uint64_t *tasks_counted, void *stream);
 
 /* Autotuner: runs the batch once per candidate CTA shape (64..512
- * threads) and slab size (2..64 KB), each at the most resident CTAs per SM
+ * threads) and slab size (2..32 KB), each at the most resident CTAs per SM
  * that fit, and returns the fastest in *best (and its time in *best_ms).
  * The outputs hold a correct result afterwards. Synchronises `stream`. The
  * paper sizes its shared stack statically (Sec. 5.3, Sec. 7); this picks

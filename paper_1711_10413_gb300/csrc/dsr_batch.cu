@@ -232,11 +232,11 @@ __global__ void __launch_bounds__(MAXT, MINB) batch_kernel(const __grid_constant
 
 using BatchFn = void (*)(BatchArgs);
 
-// Three register budgets: small CTAs held to 40 registers so that many of
+// Three register budgets: small CTAs held to 32 registers so that many of
 // them (many tasks in flight) fit an SM; the others up to 64.
 template <class P>
 BatchFn pick_batch(uint32_t threads) {
-  if (threads <= 128) return batch_kernel<P, 128, 12>;
+  if (threads <= 128) return batch_kernel<P, 128, 16>;
   if (threads <= 256) return batch_kernel<P, 256, 4>;
   return batch_kernel<P, 1024, 1>;
 }
@@ -527,8 +527,8 @@ extern "C" int32_t dsr_autotune(dsr_ctx *ctx, const dsr_region_desc *descs_dev, 
   cudaEventCreate(&z);
   float best_t = 1e30f;
   dsr_batch_tuning best_c = {256, 16384, 0, 0};
-  const uint32_t kThreads[] = {64, 128, 256, 512};
-  const uint32_t kSlabs[] = {2048, 8192, 16384, 32768, 65536};
+  const uint32_t kThreads[] = {64, 96, 128, 192, 256, 512};
+  const uint32_t kSlabs[] = {2048, 4096, 8192, 16384, 32768};
   for (uint32_t th : kThreads)
     for (uint32_t sl : kSlabs) {
       dsr_batch_tuning t = {th, sl, 0, 0};

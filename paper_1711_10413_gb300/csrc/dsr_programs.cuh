@@ -40,6 +40,11 @@ struct ProgPaperScalars {
     pop(s, f, d.frame_bytes[0]);
   }
 
+  __device__ static void run(const Env &e, uint32_t work, uint32_t first, uint32_t W,
+                             uint32_t n, uint32_t arg) {
+    run_threads<ProgPaperScalars>(e, work, first, W, n, arg);
+  }
+
   __device__ static void body(const Env &e, uint32_t, uint32_t tid, uint32_t n, uint32_t) {
     const uint8_t *f = ctrl()->frames[0].ptr;
     const uint32_t nv = e.d->param;
@@ -68,6 +73,11 @@ struct ProgPaperArrays {
     __syncwarp();
     parallel<ProgPaperArrays>(e, 0, region_width(d), 0);
     pop(s, f, d.frame_bytes[0]);
+  }
+
+  __device__ static void run(const Env &e, uint32_t work, uint32_t first, uint32_t W,
+                             uint32_t n, uint32_t arg) {
+    run_threads<ProgPaperArrays>(e, work, first, W, n, arg);
   }
 
   __device__ static void body(const Env &e, uint32_t, uint32_t tid, uint32_t n, uint32_t) {
@@ -115,6 +125,11 @@ struct ProgScalars {
       parallel<ProgScalars>(e, 0, width, r);
       pop(s, f, 16);
     }
+  }
+
+  __device__ static void run(const Env &e, uint32_t work, uint32_t first, uint32_t W,
+                             uint32_t n, uint32_t arg) {
+    run_threads<ProgScalars>(e, work, first, W, n, arg);
   }
 
   __device__ static void body(const Env &e, uint32_t, uint32_t tid, uint32_t n, uint32_t r) {
@@ -174,6 +189,11 @@ struct ProgNested {
       if (lane_id() == 0) ctrl()->chk[k - 1] = reinterpret_cast<const uint32_t *>(f)[15];
       pop(s, f, d.frame_bytes[k - 1]);
     }
+  }
+
+  __device__ static void run(const Env &e, uint32_t work, uint32_t first, uint32_t W,
+                             uint32_t n, uint32_t arg) {
+    run_threads<ProgNested>(e, work, first, W, n, arg);
   }
 
   __device__ static void body(const Env &e, uint32_t work, uint32_t tid, uint32_t n,
@@ -255,6 +275,11 @@ struct ProgSweep {
     pop(s, f, S);
   }
 
+  __device__ static void run(const Env &e, uint32_t work, uint32_t first, uint32_t W,
+                             uint32_t n, uint32_t arg) {
+    run_threads<ProgSweep>(e, work, first, W, n, arg);
+  }
+
   __device__ static void body(const Env &e, uint32_t, uint32_t tid, uint32_t n, uint32_t) {
     const float *arr = reinterpret_cast<const float *>(ctrl()->frames[0].ptr);
     const uint32_t L = ctrl()->frames[0].bytes / 4u;
@@ -314,6 +339,44 @@ struct ProgHetero {
     }
     if (lane_id() == 0) ctrl()->chk[D - 1] = frame_words(D - 1)[0];
     for (uint32_t k = D; k >= 1; --k) pop(s, ctrl()->frames[k - 1].ptr, d.frame_bytes[k - 1]);
+  }
+
+  // The worker's virtual threads with the frame pointers and sizes read
+  // once per region instead of once per thread.
+  __device__ static void run(const Env &e, uint32_t work, uint32_t first, uint32_t W,
+                             uint32_t n, uint32_t k) {
+    const Ctrl *c = ctrl();
+    if (work == kUpdate) {
+      uint32_t *f = reinterpret_cast<uint32_t *>(c->frames[k - 1].ptr);
+      const uint32_t L = c->frames[k - 1].bytes / 4u;
+      for (uint32_t v = first; v < n && v < L; v += W)
+        for (uint32_t w = v; w < L; w += n) f[w] = mix32(f[w] + w);
+      return;
+    }
+    const uint32_t *f[DSR_MAX_DEPTH];
+    uint32_t L[DSR_MAX_DEPTH];
+#pragma unroll
+    for (uint32_t m = 0; m < DSR_MAX_DEPTH; ++m) {
+      f[m] = m < k ? reinterpret_cast<const uint32_t *>(c->frames[m].ptr) : nullptr;
+      L[m] = m < k ? c->frames[m].bytes / 4u : 0u;
+    }
+    uint32_t *o = reinterpret_cast<uint32_t *>(e.out + e.d->out_offset) +
+                  static_cast<uint64_t>(e.team) * n;
+    // threads at or past every frame's end have no elements: their sum is 0
+    const uint32_t Lmax = max(max(L[0], L[1]), max(L[2], L[3]));
+    uint32_t v = first;
+    for (; v < n && v < Lmax; v += W) {
+      uint32_t acc = 0;
+#pragma unroll
+      for (uint32_t m = 0; m < DSR_MAX_DEPTH; ++m) {
+        if (m < k) {
+          const uint32_t tag = (m + 1u) << 24;
+          for (uint32_t w = v; w < L[m]; w += n) acc += mix32(f[m][w] ^ tag ^ w);
+        }
+      }
+      o[v] = acc;
+    }
+    for (; v < n; v += W) o[v] = 0u;
   }
 
   __device__ static void body(const Env &e, uint32_t work, uint32_t tid, uint32_t n,

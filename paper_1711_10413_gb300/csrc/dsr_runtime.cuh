@@ -491,9 +491,18 @@ __device__ __forceinline__ void key_in_place(uint8_t *dst, uint32_t bytes, uint3
 
 // Sum of the words [0, words) of a frame (master warp; wrap-around sum, so
 // the lane split gives the same value as one thread summing in order).
+// 16-byte loads when the frame is 16-byte aligned.
 __device__ __forceinline__ uint32_t frame_sum(const uint32_t *f, uint32_t words) {
-  uint32_t v = 0;
-  for (uint32_t w = lane_id(); w < words; w += 32u) v += f[w];
+  uint32_t v = 0, w0 = 0;
+  if ((reinterpret_cast<uintptr_t>(f) & 15u) == 0) {
+    const uint4 *f4 = reinterpret_cast<const uint4 *>(f);
+    for (uint32_t i = lane_id(); i < words / 4u; i += 32u) {
+      const uint4 x = f4[i];
+      v += x.x + x.y + x.z + x.w;
+    }
+    w0 = words & ~3u;
+  }
+  for (uint32_t w = w0 + lane_id(); w < words; w += 32u) v += f[w];
   return warp_sum(v);
 }
 
@@ -542,9 +551,18 @@ __device__ __forceinline__ void worker_loop(const Env &e0) {
       e.d = &c->desc;
       e.team = c->team;
     }
-    for (uint32_t v = threadIdx.x; v < n; v += W) P::body(e, work, v, n, arg);
+    P::run(e, work, threadIdx.x, W, n, arg);
     named_arrive(kJoinBar, team_threads());
   }
+}
+
+// A worker's share of a parallel region: its virtual threads v = first,
+// first + W, ... below n, each running the body. Programs may provide their
+// own `run` that hoists per-region values out of the loop over v.
+template <class P>
+__device__ __forceinline__ void run_threads(const Env &e, uint32_t work, uint32_t first,
+                                            uint32_t W, uint32_t n, uint32_t arg) {
+  for (uint32_t v = first; v < n; v += W) P::body(e, work, v, n, arg);
 }
 
 __device__ __forceinline__ void terminate_workers() {

@@ -36,6 +36,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <atomic>
 #include <chrono>
 #include <cstring>
@@ -65,10 +66,14 @@ struct HostShared {  // pinned, mapped
   unsigned long long pad[14];
 };
 
-struct alignas(16) SlotState {
+static_assert(offsetof(dsr_region_desc, teams) == 4, "the doorbell reads teams as word 1");
+
+struct alignas(32) SlotState {
   unsigned long long claim;  // (sequence << 32) | next team to hand out
+  unsigned int teams;        // the request's teams (written by the doorbell)
   unsigned int done;         // teams finished
   int status;                // worst team status
+  unsigned int pad[3];
 };
 
 struct ServeWs {  // device workspace header
@@ -124,20 +129,52 @@ __device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long
   return v;
 }
 
-__device__ __forceinline__ void st_release_gpu(unsigned long long *p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+// Claim a run of teams of request r if it has teams left (lane 0): about
+// a sixteenth of what is left, at most kChunk, at least one. `advance` reports
+// that r has no team left to hand out (all claimed, or r is done).
+constexpr uint32_t kChunk = 4;
+
+__device__ __forceinline__ bool claim_in(const ServeArgs &a, unsigned long long r,
+                                         uint32_t *team, uint32_t *count, bool *advance) {
+  const uint32_t slot = static_cast<uint32_t>(r % a.capacity);
+  SlotState *st = a.slots + slot;
+  const uint32_t T = *reinterpret_cast<volatile const unsigned int *>(&st->teams);
+  unsigned long long w = ld_relaxed_gpu(&st->claim);
+  *advance = false;
+  for (int cas = 0; cas < 4; ++cas) {
+    if ((w >> 32) != (r & 0xffffffffull) || static_cast<uint32_t>(w) >= T) {
+      *advance = true;
+      return false;
+    }
+    const uint32_t left = T - static_cast<uint32_t>(w);
+    const uint32_t g = min(kChunk, max(1u, left / 16u));
+    const unsigned long long prev = atomicCAS(&st->claim, w, w + g);
+    if (prev == w) {
+      *team = static_cast<uint32_t>(w);
+      *count = g;
+      return true;
+    }
+    w = prev;
+  }
+  return false;
 }
 
-// Claim one team of a submitted request (master warp). Returns false when
-// no team is available now. The CTA looks at the kWindow oldest requests in
-// flight, starting at one that depends on its block index.
+// Claim teams of a submitted request (master warp). Returns false when
+// no team is available now. The CTA first tries the request it ran last
+// (`hint`), then looks at the kWindow oldest requests in flight, starting at
+// one that depends on its block index, so claims spread over the window.
 constexpr uint32_t kWindow = 32;
 
-__device__ __forceinline__ bool claim(const ServeArgs &a, unsigned long long *seq,
-                                      uint32_t *team) {
+__device__ __forceinline__ bool claim(const ServeArgs &a, unsigned long long hint,
+                                      unsigned long long *seq, uint32_t *team, uint32_t *count) {
   unsigned long long out_seq = 0;
-  uint32_t out_team = 0, got = 0;
+  uint32_t out_team = 0, out_count = 0, got = 0;
   if (lane_id() == 0) {
+    bool adv;
+    if (hint != ~0ull && claim_in(a, hint, &out_team, &out_count, &adv)) {
+      got = 1;
+      out_seq = hint;
+    }
     for (int tries = 0; tries < 8 && !got; ++tries) {
       const unsigned long long h = ld_relaxed_gpu(&a.ws->head);
       const unsigned long long tail = ld_acquire_gpu(&a.ws->tail);
@@ -146,23 +183,11 @@ __device__ __forceinline__ bool claim(const ServeArgs &a, unsigned long long *se
       const uint32_t start = (blockIdx.x * 7u + static_cast<uint32_t>(tries)) % n;
       for (uint32_t j = 0; j < n && !got; ++j) {
         const unsigned long long r = h + (start + j) % n;
-        const uint32_t slot = static_cast<uint32_t>(r % a.capacity);
-        const uint32_t T = a.dring[slot].teams;
-        unsigned long long w = ld_relaxed_gpu(&a.slots[slot].claim);
-        for (int cas = 0; cas < 4; ++cas) {
-          if ((w >> 32) != (r & 0xffffffffull) || static_cast<uint32_t>(w) >= T) {
-            // r's teams are all handed out (or r is done): the head may pass it
-            if (r == h) atomicCAS(&a.ws->head, h, h + 1);
-            break;
-          }
-          const unsigned long long prev = atomicCAS(&a.slots[slot].claim, w, w + 1);
-          if (prev == w) {
-            got = 1;
-            out_seq = r;
-            out_team = static_cast<uint32_t>(w);
-            break;
-          }
-          w = prev;
+        if (claim_in(a, r, &out_team, &out_count, &adv)) {
+          got = 1;
+          out_seq = r;
+        } else if (adv && r == h) {
+          atomicCAS(&a.ws->head, h, h + 1);  // the head may pass a handed-out request
         }
       }
     }
@@ -170,6 +195,7 @@ __device__ __forceinline__ bool claim(const ServeArgs &a, unsigned long long *se
   got = __shfl_sync(0xffffffffu, got, 0);
   *seq = __shfl_sync(0xffffffffu, out_seq, 0);
   *team = __shfl_sync(0xffffffffu, out_team, 0);
+  *count = __shfl_sync(0xffffffffu, out_count, 0);
   return got != 0;
 }
 
@@ -204,8 +230,9 @@ __global__ void __launch_bounds__(MAXT, MINB) serve_kernel(const __grid_constant
       if (t > last) {
         for (unsigned long long r = last + lane / 4u; r < t; r += 8u) {
           const uint32_t slot = static_cast<uint32_t>(r % a.capacity);
-          reinterpret_cast<uint4 *>(a.dring + slot)[lane & 3u] =
-              reinterpret_cast<const uint4 *>(a.ring + slot)[lane & 3u];
+          const uint4 q = reinterpret_cast<const uint4 *>(a.ring + slot)[lane & 3u];
+          reinterpret_cast<uint4 *>(a.dring + slot)[lane & 3u] = q;
+          if ((lane & 3u) == 0) a.slots[slot].teams = q.y;  // dsr_region_desc::teams
         }
         __threadfence();
         __syncwarp();
@@ -233,10 +260,14 @@ __global__ void __launch_bounds__(MAXT, MINB) serve_kernel(const __grid_constant
   bool first = true;
   uint64_t idle_since = globaltimer();
   uint32_t backoff = 256;
+  unsigned long long hint = ~0ull;
+  unsigned long long cached = ~0ull;  // request whose descriptor is in the control block
+  bool cached_ok = false;
   for (;;) {
     unsigned long long seq;
-    uint32_t team;
-    if (!claim(a, &seq, &team)) {
+    uint32_t team0, count;
+    if (!claim(a, hint, &seq, &team0, &count)) {
+      hint = ~0ull;
       // nothing to run: leave when asked to stop (all submitted work has
       // been claimed) or after the idle timeout; otherwise back off
       unsigned long long stop = 0;
@@ -259,41 +290,50 @@ __global__ void __launch_bounds__(MAXT, MINB) serve_kernel(const __grid_constant
       continue;
     }
     backoff = 256;
+    hint = seq;
     idle_since = globaltimer();
     const uint32_t slot = static_cast<uint32_t>(seq % a.capacity);
-    __syncwarp();
-    if (lane < 4)
-      reinterpret_cast<uint4 *>(&c->desc)[lane] =
-          reinterpret_cast<const uint4 *>(a.dring + slot)[lane];
-    if (lane == 0) c->team = team;
-    __syncwarp();
-    e.d = &c->desc;
-    e.team = team;
-    team_setup(s, a.slab_bytes, ovf, a.ovf_per_cta, a.timeout_ns, first);
-    first = false;
+    if (seq != cached) {
+      __syncwarp();
+      if (lane < 4)
+        reinterpret_cast<uint4 *>(&c->desc)[lane] =
+            reinterpret_cast<const uint4 *>(a.dring + slot)[lane];
+      __syncwarp();
+      cached = seq;
+      cached_ok = c->desc.program == P::kProgram && shape_error(c->desc) == 0 &&
+                  fits(c->desc, a.image_bytes, a.out_bytes, a.n_status);
+    }
     const dsr_region_desc &d = c->desc;
-    int32_t st;
-    if (d.program != P::kProgram || shape_error(d) != 0 ||
-        !fits(d, a.image_bytes, a.out_bytes, a.n_status)) {
-      st = DSR_ERR_INVALID;
-      if (lane == 0) {
-        atomicAdd(&a.ws->errors, 1u);
-        const uint64_t si = static_cast<uint64_t>(d.status_index) + team;
-        if (si < a.n_status) {
-          dsr_team_status r = {};
-          r.status = DSR_ERR_INVALID;
-          a.status[si] = r;
+    int32_t worst = DSR_OK;
+    for (uint32_t team = team0; team < team0 + count; ++team) {
+      if (lane == 0) c->team = team;
+      e.d = &c->desc;
+      e.team = team;
+      team_setup(s, a.slab_bytes, ovf, a.ovf_per_cta, a.timeout_ns, first);
+      first = false;
+      int32_t st;
+      if (!cached_ok) {
+        st = DSR_ERR_INVALID;
+        if (lane == 0) {
+          atomicAdd(&a.ws->errors, 1u);
+          const uint64_t si = static_cast<uint64_t>(d.status_index) + team;
+          if (si < a.n_status) {
+            dsr_team_status r = {};
+            r.status = DSR_ERR_INVALID;
+            a.status[si] = r;
+          }
         }
+      } else {
+        P::master(e, s);
+        st = s.status();
+        team_report(e, s, a.status);
       }
-    } else {
-      P::master(e, s);
-      st = s.status();
-      team_report(e, s, a.status);
+      worst = max(worst, st);
     }
     if (lane == 0) {
-      __threadfence();  // this team's outputs before its completion count
-      if (st != DSR_OK) atomicMax(&a.slots[slot].status, st);
-      const uint32_t done = atomicAdd(&a.slots[slot].done, 1u) + 1u;
+      __threadfence();  // these teams' outputs before their completion count
+      if (worst != DSR_OK) atomicMax(&a.slots[slot].status, worst);
+      const uint32_t done = atomicAdd(&a.slots[slot].done, count) + count;
       if (done == d.teams) {
         // the request's last team: recycle the slot for request seq +
         // capacity, then publish the completion to the host
@@ -319,7 +359,7 @@ using ServeFn = void (*)(ServeArgs);
 
 template <class P>
 ServeFn pick_serve(uint32_t threads) {
-  if (threads <= 128) return serve_kernel<P, 128, 12>;
+  if (threads <= 128) return serve_kernel<P, 128, 8>;
   if (threads <= 256) return serve_kernel<P, 256, 4>;
   return serve_kernel<P, 1024, 1>;
 }
@@ -350,6 +390,7 @@ __global__ void serve_init(ServeWs *ws, SlotState *slots, uint32_t capacity) {
   }
   if (i < capacity) {
     slots[i].claim = static_cast<unsigned long long>(i) << 32;
+    slots[i].teams = 0;
     slots[i].done = 0;
     slots[i].status = 0;
   }

@@ -232,6 +232,9 @@ def measure_forms(dsr, torch, device, flush):
     distinct, n = 20000, 100000
     warm = n // 10
     sw = wl.hetero(n_instances=distinct)
+    # the served form's overflow pool: 4 GiB, 1 MiB for each of 4096 CTAs
+    pool_per_cta, pool_ctas = 1 << 20, 4096
+    rt.configure(16384, pool_per_cta, pool_ctas)
     served = {}
     for shape in SERVE_SHAPES:
         # The server runs its own CTA shape: with requests arriving one at a
@@ -261,8 +264,8 @@ def measure_forms(dsr, torch, device, flush):
                                    p99_us=float(np.percentile(lat, 99)) / 1e3,
                                    sustained_regions_per_s=m / (el * 1e-9))
     forms["served"] = dict(workload="hetero_poisson_%d_requests_%d_distinct" % (n, distinct),
-                           warmup_dropped=warm, overflow_pool_bytes=
-                           3 * 32768 * 4096, server=served, per_request_launch=launched)
+                           warmup_dropped=warm, overflow_pool_bytes=pool_per_cta * pool_ctas,
+                           server=served, per_request_launch=launched)
     rt.close()
     return forms
 

@@ -156,39 +156,103 @@ struct ProgNested {
   static constexpr bool kDense = true;
   enum : uint32_t { kUpdate = 0, kInner = 1 };
 
+  // A frame in the slab is published to the workers as its byte offset in
+  // shared memory with kSmemArg set (the parallel call's argument word);
+  // otherwise the argument is the level k and the workers read the frame
+  // table. kInner with kSmemArg: all D frames lie back to back from there.
+  static constexpr uint32_t kSmemArg = 0x80000000u;
+  // Every level's frame is 16 scalars and int32[256] (descriptors of this
+  // program are checked to say so).
+  static constexpr uint32_t kFrameBytes = 1088u;
+
   __device__ static void master(const Env &e, Stack &s) {
-    const dsr_region_desc &d = *e.d;
-    const uint32_t D = d.depth, width = region_width(d);
-    const uint8_t *timg = e.images + d.image_offset + static_cast<uint64_t>(e.team) * D * 1088u;
+    const uint32_t D = e.d->depth;
     // all levels' images at once, into the slab slots the pushes will take
-    const uint8_t *expect = slab_base() + s.sp;
-    const bool staged = stage(s, timg, D * 1088u);
-    if (!staged && lane_id() == 0) prefetch_l2(timg, D * 1088u);
+    // (from byte `x0` of shared memory on)
+    const uint32_t x0 = kCtrlBytes + s.sp;
+    if (stage(s, image(e, 1), D * 1088u)) {
+      levels<true>(e, s, x0);
+    } else {
+      if (lane_id() == 0) prefetch_l2(image(e, 1), D * 1088u);
+      levels<false>(e, s, x0);
+    }
+  }
+
+  // The D levels. kStaged: the images were staged from x0 on, so level k's
+  // frame takes the slab slot x0 + 1088 (k - 1) (pushes are in order and
+  // the staged total fitted the slab) and is filled once its slot is keyed.
+  template <bool kStaged>
+  __device__ static void levels(const Env &e, Stack &s, uint32_t x0) {
+    const dsr_region_desc &d = *e.d;
+    const uint32_t D = d.depth;
+    uint32_t carry = 0;  // c_{k-1}, the sum the previous level left in word 15
     for (uint32_t k = 1; k <= D; ++k) {
       bool sm;
-      uint8_t *f = push(s, d.frame_bytes[k - 1], &sm);
+      uint8_t *f = push(s, kFrameBytes, &sm);
       if (!f) return;
-      const uint32_t key = mix32(e.team * 8u + k);
-      if (staged && k == 1) wait_staged(s);
-      if (staged && f == expect + (k - 1) * 1088u)
-        key_in_place(f, 1088u, key);
-      else
-        fill<!kDense>(s, f, sm, timg + (k - 1) * 1088u, 1088u, key);
+      const uint32_t off = static_cast<uint32_t>(f - dsr_smem);  // meaningful when sm
+      if (kStaged) {
+        if (!sm || off != x0 + (k - 1) * 1088u) {
+          set_status(s, DSR_ERR_INVALID);  // not where staging put the image
+          return;
+        }
+        if (k == 1) {
+          // the staged images land together; key every level's slot now
+          wait_staged(s);
+          key_levels(dsr_smem + x0, D, e.team);
+        }
+      } else {
+        fill<!kDense>(s, f, sm, image(e, k), 1088u, mix32(e.team * 8u + k));
+      }
       if (s.status() != DSR_OK) return;
-      if (k > 1 && lane_id() == 0) reinterpret_cast<uint32_t *>(f)[0] ^= frame_words(k - 2)[15];
+      if (lane_id() == 0) {
+        uint32_t *w = reinterpret_cast<uint32_t *>(f);
+        if (k > 1) w[0] ^= carry;
+        // the last level's word 15 is final here (its region writes only
+        // the output); earlier levels record their sums below
+        if (k == D) ctrl()->chk[k - 1] = w[15];
+      }
       __syncwarp();
-      parallel<ProgNested>(e, k < D ? kUpdate : kInner, width, k);
+      uint32_t arg = k;
+      if (k < D && sm) arg = kSmemArg | off;
+      if (kStaged && k == D) arg = kSmemArg | x0;
+      parallel<ProgNested>(e, k < D ? kUpdate : kInner, region_width(d), arg);
       if (k < D) {
-        const uint32_t sum = frame_sum(reinterpret_cast<const uint32_t *>(f) + 16, 256);
-        if (lane_id() == 0) reinterpret_cast<uint32_t *>(f)[15] = sum;
+        carry = frame_sum(reinterpret_cast<const uint32_t *>(f) + 16, 256);
+        if (lane_id() == 0) {
+          reinterpret_cast<uint32_t *>(f)[15] = carry;
+          ctrl()->chk[k - 1] = carry;
+        }
         __syncwarp();
       }
     }
     for (uint32_t k = D; k >= 1; --k) {
-      const uint8_t *f = ctrl()->frames[k - 1].ptr;
-      if (lane_id() == 0) ctrl()->chk[k - 1] = reinterpret_cast<const uint32_t *>(f)[15];
-      pop(s, f, d.frame_bytes[k - 1]);
+      const uint8_t *p = kStaged ? dsr_smem + x0 + (k - 1) * 1088u : ctrl()->frames[k - 1].ptr;
+      pop(s, p, kFrameBytes);
     }
+  }
+
+  // The image of level k of this team (1088 bytes).
+  __device__ static const uint8_t *image(const Env &e, uint32_t k) {
+    return e.images + e.d->image_offset +
+           (static_cast<uint64_t>(e.team) * e.d->depth + (k - 1)) * 1088u;
+  }
+
+  // XOR level m's slot (1088 bytes from base + 1088 m) with
+  // mix32(team*8 + m + 1), for every level at once (master warp).
+  __device__ static void key_levels(uint8_t *base, uint32_t D, uint32_t team) {
+    uint4 *v = reinterpret_cast<uint4 *>(base);
+    const uint32_t n = D * 68u;  // 1088 / 16 vectors per level
+    for (uint32_t i = lane_id(); i < n; i += 32u) {
+      const uint32_t key = mix32(team * 8u + i / 68u + 1u);
+      uint4 x = v[i];
+      x.x ^= key;
+      x.y ^= key;
+      x.z ^= key;
+      x.w ^= key;
+      v[i] = x;
+    }
+    __syncwarp();
   }
 
   __device__ static void run(const Env &e, uint32_t work, uint32_t first, uint32_t W,
@@ -196,10 +260,45 @@ struct ProgNested {
     run_threads<ProgNested>(e, work, first, W, n, arg);
   }
 
+  // The innermost region over groups g = tid, tid + n, ... < G of 4
+  // consecutive elements j0 = 4g .. 4g + 3, with the kD frames back to back
+  // in shared memory from byte `base` on. arr[j & 255] and s[j & 15] of a
+  // group are 4 consecutive words (256 and 16 are multiples of 4), read as
+  // one 16-byte vector each; the 4 outputs are one 16-byte store. E is a
+  // multiple of 4, so e0 = team*E + j0 is too and e0 + i = e0 | i.
+  template <uint32_t kD>
+  __device__ static void inner4(uint32_t base, uint32_t *o, uint32_t ebase, uint32_t tid,
+                                uint32_t n, uint32_t G) {
+    const uint8_t *fs = dsr_smem + base;  // level 0's scalars; its array 64 bytes on
+    for (uint32_t g = tid; g < G; g += n) {
+      const uint32_t j0 = g << 2;
+      const uint32_t oa = 64u + 4u * (j0 & 255u), os = 4u * (j0 & 15u);
+      uint4 acc = make_uint4(0, 0, 0, 0);
+#pragma unroll
+      for (uint32_t m = 0; m < kD; ++m) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(fs + m * kFrameBytes + oa);
+        const uint4 sv = *reinterpret_cast<const uint4 *>(fs + m * kFrameBytes + os);
+        acc.x += a.x ^ sv.x;
+        acc.y += a.y ^ sv.y;
+        acc.z += a.z ^ sv.z;
+        acc.w += a.w ^ sv.w;
+      }
+      const uint32_t e0 = ebase + j0;
+      uint4 r;
+      r.x = mix32(e0 ^ acc.x);
+      r.y = mix32((e0 | 1u) ^ acc.y);
+      r.z = mix32((e0 | 2u) ^ acc.z);
+      r.w = mix32((e0 | 3u) ^ acc.w);
+      *reinterpret_cast<uint4 *>(o + j0) = r;
+    }
+  }
+
   __device__ static void body(const Env &e, uint32_t work, uint32_t tid, uint32_t n,
                               uint32_t k) {
     if (work == kUpdate) {
-      uint32_t *arr = reinterpret_cast<uint32_t *>(ctrl()->frames[k - 1].ptr) + 16;
+      uint32_t *arr = (k & kSmemArg ? reinterpret_cast<uint32_t *>(dsr_smem + (k & ~kSmemArg))
+                                    : reinterpret_cast<uint32_t *>(ctrl()->frames[k - 1].ptr)) +
+                      16;
       for (uint32_t i = tid; i < 256u; i += n) arr[i] = mix32(arr[i] + i);
       return;
     }
@@ -207,42 +306,16 @@ struct ProgNested {
     uint32_t *o = reinterpret_cast<uint32_t *>(e.out + e.d->out_offset) +
                   static_cast<uint64_t>(e.team) * E;
     const uint32_t ebase = e.team * E;
-    bool all_smem = true;
-    for (uint32_t m = 0; m < D; ++m) all_smem &= ctrl()->frames[m].in_smem != 0;
-    // Each element j is written by exactly one worker; the workers take
-    // groups of 4 consecutive elements (16-byte frame reads and output
-    // stores) when E is a multiple of 4. arr[j & 255] and s[j & 15] of a
-    // group are 4 consecutive words (256 and 16 are multiples of 4).
-    if ((E & 3u) == 0 && all_smem) {
-      // frames addressed as byte offsets into the team's shared memory
-      uint32_t fo[DSR_MAX_DEPTH];
-#pragma unroll
-      for (uint32_t m = 0; m < DSR_MAX_DEPTH; ++m)
-        fo[m] = m < D ? static_cast<uint32_t>(ctrl()->frames[m].ptr - dsr_smem) : 0u;
-      for (uint32_t g = tid; g < (E >> 2); g += n) {
-        const uint32_t j0 = g << 2;
-        uint4 acc = make_uint4(0, 0, 0, 0);
-#pragma unroll
-        for (uint32_t m = 0; m < DSR_MAX_DEPTH; ++m) {
-          if (m < D) {
-            const uint4 a = *reinterpret_cast<const uint4 *>(dsr_smem + fo[m] + 64u +
-                                                             4u * (j0 & 255u));
-            const uint4 sv = *reinterpret_cast<const uint4 *>(dsr_smem + fo[m] + 4u * (j0 & 15u));
-            acc.x += a.x ^ sv.x;
-            acc.y += a.y ^ sv.y;
-            acc.z += a.z ^ sv.z;
-            acc.w += a.w ^ sv.w;
-          }
-        }
-        const uint32_t e0 = ebase + j0;
-        uint4 r;
-        r.x = mix32(e0 ^ acc.x);
-        r.y = mix32((e0 + 1u) ^ acc.y);
-        r.z = mix32((e0 + 2u) ^ acc.z);
-        r.w = mix32((e0 + 3u) ^ acc.w);
-        *reinterpret_cast<uint4 *>(o + j0) = r;
+    // Each element j is written by exactly one worker; with E a multiple of
+    // 4 and the frames in the slab, the workers take groups of 4.
+    if ((E & 3u) == 0 && (k & kSmemArg)) {
+      const uint32_t base = k & ~kSmemArg;
+      switch (D) {
+        case 1: inner4<1>(base, o, ebase, tid, n, E >> 2); return;
+        case 2: inner4<2>(base, o, ebase, tid, n, E >> 2); return;
+        case 3: inner4<3>(base, o, ebase, tid, n, E >> 2); return;
+        default: inner4<4>(base, o, ebase, tid, n, E >> 2); return;
       }
-      return;
     }
     for (uint32_t j = tid; j < E; j += n) {
       uint32_t acc = 0;

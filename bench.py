@@ -6,8 +6,11 @@ threads, 3 nested levels each pushing a 1088-byte frame (16 int32 scalars
 + int32[256]), 4M int32 output -- one region instance per step, launched
 through the C ABI. Metric: regions/s, with push+pop/s beside it.
 
-The same JSON line also carries the other launch forms, each on its own
-configuration (`--forms none` skips them):
+The same JSON line also carries the other configurations and launch forms
+(`--forms none` skips them):
+  sweep    - 512 teams x 128 threads, one fp32 frame of 64 B .. 192 KiB per
+             team, in the shared-memory slab and in the overflow slab: time,
+             HBM GB/s, occupancy and shared memory per team for each;
   scalars  - 1 team x 128 threads, 1000 sequential regions: one launch that
              runs them all against 1000 launches of one region each;
   batched  - 10,000 heterogeneous instances (log-uniform teams and frame
@@ -189,8 +192,67 @@ def _event_ms(torch, fn, reps, flush=None):
     return float(np.median(out))
 
 
-def measure_forms(dsr, torch, device, flush):
+def smem_peak_gbs(sm_count: int, sm_mhz: float = 2070.0) -> float:
+    """Shared-memory bandwidth bound: 128 bytes per clock per SM (32 banks
+    of 4 bytes) at the maximum SM clock."""
+    return sm_count * 128.0 * sm_mhz * 1e6 / 1e9
+
+
+def hetero_stack_bytes(regions) -> int:
+    """Stack bytes the hetero program moves by its definition, summed over
+    teams: each level's frame is written once by its push, read and written
+    once by a non-innermost region, read once by the master's sum after
+    that region, and read once by the innermost region."""
+    total = 0
+    for r in regions:
+        fb = list(r.frame_bytes)[: r.depth]
+        total += r.teams * (2 * sum(fb) + 3 * sum(fb[:-1]))
+    return total
+
+
+def measure_sweep(dsr, torch, device, flush, hbm_gbs):
+    """Config 3: one fp32 frame per team, 512 teams x 128 threads, for each
+    frame size placed in the shared-memory slab (when one CTA can hold it)
+    and in the global overflow slab; HBM bytes per launch = images read +
+    outputs + statuses."""
+    teams, threads = 512, 128
+    rt = dsr.Runtime(device, slab_bytes=0, overflow_bytes_per_team=max(wl.SWEEP_SIZES),
+                     max_teams=teams)
+    res = []
+    for S in wl.SWEEP_SIZES:
+        work = wl.sweep(S, teams=teams, threads=threads)
+        region = work.regions[0]
+        images, out, status = rt.device_buffers(work)
+        for where in ("smem", "overflow"):
+            if where == "smem":
+                if S + 384 > 232448:
+                    continue
+                rt.configure(S, 0, 0)
+            else:
+                rt.configure(0, S, teams)
+            occ = rt.occupancy(region)
+            ms = _event_ms(torch, lambda: dsr.dsr_launch_region(rt.ctx, region, images, out,
+                                                                status), 10, flush)
+            st = status.cpu().numpy().view(dsr.TEAM_STATUS_DTYPE)
+            hbm = teams * S + teams * (threads - 32) * 4 + teams * 32
+            gbs = hbm / (ms * 1e-3) / 1e9
+            res.append(dict(frame_bytes=S, placement=where, us=ms * 1e3,
+                            regions_per_s=1.0 / (ms * 1e-3), hbm_bytes=hbm, hbm_gbs=gbs,
+                            hbm_frac=gbs / hbm_gbs,
+                            overflow_bytes=2 * teams * S if where == "overflow" else 0,
+                            smem_per_team=occ["smem_per_team"], ctas_per_sm=occ["ctas_per_sm"],
+                            regs_per_thread=occ["regs_per_thread"],
+                            spill_bytes_per_team=int(st["spill_bytes"].max()),
+                            bad_team_status=int((st["status"] != 0).sum())))
+        del images, out, status
+    rt.close()
+    return dict(workload="sweep_512x128", teams=teams, threads=threads, runs=res)
+
+
+def measure_forms(dsr, torch, device, flush, hbm_gbs):
     forms = {}
+    sm_count = torch.cuda.get_device_properties(device).multi_processor_count
+    forms["sweep"] = measure_sweep(dsr, torch, device, flush, hbm_gbs)
     rt = dsr.Runtime(device, slab_bytes=16384, overflow_bytes_per_team=3 * 32768, max_teams=4096)
     # config 1: 1000 sequential regions of one team
     sc = wl.scalars(n_regions=1000, teams=1, threads=128)
@@ -217,12 +279,21 @@ def measure_forms(dsr, torch, device, flush):
     err, counted = rt.batch_errors(b)
     ms_plain = _event_ms(torch, lambda: rt.launch_regions(b), 2, flush)
     st = b["status"].cpu().numpy().view(dsr.TEAM_STATUS_DTYPE)
+    stack = hetero_stack_bytes(work.regions)
+    smem_gbs = stack / (ms_batch * 1e-3) / 1e9
     forms["batched"] = dict(workload="hetero_10000_instances", instances=10000, teams=counted,
                             tuning=tuning, batched_regions_per_s=10000 / (ms_batch * 1e-3),
                             per_launch_regions_per_s=10000 / (ms_plain * 1e-3),
                             batched_push_pop_per_s=sum(r.teams * r.depth for r in work.regions)
                             / (ms_batch * 1e-3),
-                            speedup=ms_plain / ms_batch, device_rejects=err,
+                            speedup=ms_plain / ms_batch,
+                            stack_roofline=dict(bound="smem", stack_bytes=stack,
+                                                achieved=smem_gbs,
+                                                peak=smem_peak_gbs(sm_count), unit="GB/s",
+                                                frac=smem_gbs / smem_peak_gbs(sm_count),
+                                                peak_source="derived: SMs x 128 B/clk x "
+                                                            "2070 MHz"),
+                            device_rejects=err,
                             bad_team_status=int((st["status"] != 0).sum()))
     del b
     # config 5: served at several rates vs per-request launches. 100,000
@@ -318,6 +389,7 @@ def main():
 
     import torch
     import paper_1711_10413_gb300 as dsr
+    from paper_1711_10413_gb300 import shard
 
     torch.cuda.set_device(local)
     dist = None
@@ -366,12 +438,10 @@ def main():
     clk = clocks.stop()
     ms = [a.elapsed_time(b) for a, b in zip(starts, stops)]
     ms_step = float(np.mean(ms))
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = shard.max_over_ranks(ms_step, dist)   # the slowest rank's step
+    regions_done = shard.sum_over_ranks(1.0, dist)  # one region per rank per step
 
-    # parity spot check of the timed buffers (full output vs the oracle)
+    # every team of the timed launches must have ended OK with its stack empty
     status_np = status.cpu().numpy().view(dsr.TEAM_STATUS_DTYPE)
     bad_status = int((status_np["status"] != 0).sum() + (status_np["depth_final"] != 0).sum())
 
@@ -395,10 +465,7 @@ def main():
         e2e_step()
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t1) / args.steps
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = shard.max_over_ranks(e2e_s, dist)
 
     if rank != 0:
         if dist:
@@ -406,7 +473,7 @@ def main():
         return
 
     peaks = _peaks()
-    regions_per_s = world * 1000.0 / ms_step
+    regions_per_s = regions_done * 1000.0 / ms_step
     achieved = algo_bytes / (ms_step * 1e-3) / 1e9
     line = dict(
         metric="regions/s", value=regions_per_s, unit="regions/s", n_gpus=world,
@@ -418,7 +485,7 @@ def main():
         roofline=dict(bound="hbm", achieved=achieved, peak=peaks["hbm_gbs"], unit="GB/s",
                       frac=achieved / peaks["hbm_gbs"], traffic=_traffic(),
                       peak_source=peaks["source"], algorithmic_bytes=algo_bytes),
-        e2e=dict(value=world / e2e_s, unit="regions/s", h2d_bytes_per_step=int(ib),
+        e2e=dict(value=regions_done / e2e_s, unit="regions/s", h2d_bytes_per_step=int(ib),
                  d2h_bytes_per_step=int(ob + 32 * region.teams)),
         gpu_launches=args.steps,
         bracket_ms_per_step=1000.0 * bracket_s / args.steps,
@@ -426,7 +493,7 @@ def main():
         clocks=clk,
     )
     if world == 1 and args.forms == "all":
-        line["forms"] = measure_forms(dsr, torch, local, flush)
+        line["forms"] = measure_forms(dsr, torch, local, flush, peaks["hbm_gbs"])
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = time_oracle(work, slab, ovf, budget_s=args.cpu_budget)
     print(json.dumps(line))

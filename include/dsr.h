@@ -180,6 +180,24 @@ int32_t dsr_region_extent(const dsr_region_desc *d, uint64_t *image_bytes, uint6
 int32_t dsr_footprint_model(const dsr_region_desc *d, uint32_t slab_bytes, uint32_t regs,
                             dsr_footprint *out);
 
+/* What the plain launch of a descriptor gets on this GPU, measured from the
+ * compiled kernel rather than modelled: the GB300 counterpart of the
+ * paper's register counts and teams-per-SM columns (Sec. 6.2.2, Tables 2,
+ * 2b, 5, 6), which the paper reads off the compiled kernel. */
+typedef struct dsr_occupancy {
+  uint32_t threads;         /* CTA threads of the launch (one extra warp when threads == 32) */
+  uint32_t regs_per_thread; /* registers of the kernel the launch runs */
+  uint32_t smem_per_team;   /* dynamic shared memory per CTA: control block + slab */
+  uint32_t ctas_per_sm;     /* resident teams per SM (the CUDA occupancy calculator) */
+  uint32_t sm_count;        /* SMs of the device */
+  uint32_t spill_bytes;     /* bytes per team its frames put in the overflow slab */
+} dsr_occupancy;
+
+/* Occupancy of the plain launch of *d with the ctx's stack configuration
+ * (dsr_stack_init). Queries the runtime only; launches nothing. Errors:
+ * DSR_ERR_INVALID (bad descriptor, no stack configured), DSR_ERR_CUDA. */
+int32_t dsr_region_occupancy(dsr_ctx *ctx, const dsr_region_desc *d, dsr_occupancy *out);
+
 /* ---- plain launch: one CTA per team, one launch per region -------------- */
 
 /* Launch one region instance (Sec. 4: the target region is one kernel

@@ -68,6 +68,12 @@ class dsr_footprint(ctypes.Structure):
                 ("limit", ctypes.c_uint32), ("spill_bytes", ctypes.c_uint32)]
 
 
+class dsr_occupancy(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_uint32), ("regs_per_thread", ctypes.c_uint32),
+                ("smem_per_team", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("sm_count", ctypes.c_uint32), ("spill_bytes", ctypes.c_uint32)]
+
+
 TEAM_STATUS_DTYPE = np.dtype([("status", "<i4"), ("depth_final", "<u4"), ("hwm_bytes", "<u4"),
                               ("spill_bytes", "<u4"), ("chk", "<u4", (DSR_MAX_DEPTH,))])
 assert ctypes.sizeof(dsr_region_desc) == 64 and TEAM_STATUS_DTYPE.itemsize == 32
@@ -100,6 +106,7 @@ def _declare(L):
         "dsr_validate_region": (_i32, [P(dsr_region_desc), _u64, _u64, _u64]),
         "dsr_region_extent": (_i32, [P(dsr_region_desc), P(_u64), P(_u64), P(_u64)]),
         "dsr_footprint_model": (_i32, [P(dsr_region_desc), _u32, _u32, P(dsr_footprint)]),
+        "dsr_region_occupancy": (_i32, [_vp, P(dsr_region_desc), P(dsr_occupancy)]),
         "dsr_launch_region": (_i32, [_vp, P(dsr_region_desc), _vp, _u64, _vp, _u64, _vp, _u64,
                                      _vp]),
         "dsr_run_region_host": (_i32, [_vp, P(dsr_region_desc), _vp, _u64, _vp, _u64, _vp,
@@ -150,6 +157,7 @@ def build(force: bool = False) -> str:
 def exported_symbols():
     return ["dsr_create", "dsr_destroy", "dsr_last_error_string", "dsr_stack_init",
             "dsr_validate_region", "dsr_region_extent", "dsr_footprint_model",
+            "dsr_region_occupancy",
             "dsr_launch_region", "dsr_run_region_host", "dsr_batch_workspace_bytes",
             "dsr_batch_count", "dsr_launch_batch", "dsr_batch_errors", "dsr_autotune",
             "dsr_launch_regions", "dsr_launch_batch_static", "dsr_batch_static_capacity",
@@ -256,6 +264,15 @@ def dsr_footprint_model(region, slab_bytes: int, regs: int = 0) -> dict:
     f = dsr_footprint()
     _check(lib().dsr_footprint_model(ctypes.byref(d), slab_bytes, regs, ctypes.byref(f)))
     return {k: getattr(f, k) for k, _ in dsr_footprint._fields_}
+
+
+def dsr_region_occupancy(ctx: int, region) -> dict:
+    """Registers, shared memory per team and resident teams per SM of the
+    plain launch of `region` with the ctx's stack configuration."""
+    d = pack_desc(region)
+    o = dsr_occupancy()
+    _check(lib().dsr_region_occupancy(ctx, ctypes.byref(d), ctypes.byref(o)), ctx)
+    return {k: getattr(o, k) for k, _ in dsr_occupancy._fields_}
 
 
 def _nbytes(x) -> int:

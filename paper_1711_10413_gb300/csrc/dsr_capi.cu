@@ -334,6 +334,42 @@ extern "C" int32_t dsr_launch_region(dsr_ctx *ctx, const dsr_region_desc *d,
                           static_cast<cudaStream_t>(stream));
 }
 
+extern "C" int32_t dsr_region_occupancy(dsr_ctx *ctx, const dsr_region_desc *d,
+                                        dsr_occupancy *out) {
+  if (!ctx) return dsr_fail(nullptr, DSR_ERR_INVALID, "null ctx");
+  if (!out) return dsr_fail(ctx, DSR_ERR_INVALID, "null output");
+  if (!ctx->stack_ready) return dsr_fail(ctx, DSR_ERR_INVALID, "dsr_stack_init not called");
+  const char *why;
+  if (dsr_check_shape(d, &why) != DSR_OK) return dsr_fail(ctx, DSR_ERR_INVALID, "%s", why);
+  const uint32_t block = d->threads > 32u ? d->threads : 64u;
+  const void *k = reinterpret_cast<const void *>(plain_kernel_for(d->program, block));
+  const uint32_t smem = kCtrlBytes + ctx->slab_bytes;
+  cudaFuncAttributes a{};
+  int per_sm = 0;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, static_cast<int>(block),
+                                                      static_cast<size_t>(smem));
+  if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "occupancy query");
+  // frames in push order, first fit into the slab, else the overflow slab
+  uint64_t sp = 0, spill = 0;
+  for (uint32_t i = 0; i < d->depth; ++i) {
+    const uint64_t fp = dsr::pad16(d->frame_bytes[i]);
+    if (sp + fp <= ctx->slab_bytes)
+      sp += fp;
+    else
+      spill += fp;
+  }
+  out->threads = block;
+  out->regs_per_thread = static_cast<uint32_t>(a.numRegs);
+  out->smem_per_team = smem;
+  out->ctas_per_sm = static_cast<uint32_t>(per_sm);
+  out->sm_count = static_cast<uint32_t>(ctx->sm_count);
+  out->spill_bytes = static_cast<uint32_t>(spill);
+  return DSR_OK;
+}
+
 extern "C" int32_t dsr_run_region_host(dsr_ctx *ctx, const dsr_region_desc *d,
                                        const void *images_host, uint64_t image_bytes,
                                        void *out_host, uint64_t out_bytes,

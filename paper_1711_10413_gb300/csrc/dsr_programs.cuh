@@ -357,7 +357,19 @@ struct ProgSweep {
     const float *arr = reinterpret_cast<const float *>(ctrl()->frames[0].ptr);
     const uint32_t L = ctrl()->frames[0].bytes / 4u;
     float acc = 0.0f;
-    for (uint32_t i = tid; i < L; i += n) acc = __fadd_rn(acc, arr[i]);
+    uint32_t i = tid;
+    // Eight loads in flight, then their additions one by one in index
+    // order: the sum is the same left-to-right fp32 sum, but the memory
+    // latency (shared memory, or L2/HBM for a spilled frame) is paid once
+    // per eight elements instead of once per element.
+    for (; i + 7u * n < L; i += 8u * n) {
+      float x[8];
+#pragma unroll
+      for (uint32_t u = 0; u < 8u; ++u) x[u] = arr[i + u * n];
+#pragma unroll
+      for (uint32_t u = 0; u < 8u; ++u) acc = __fadd_rn(acc, x[u]);
+    }
+    for (; i < L; i += n) acc = __fadd_rn(acc, arr[i]);
     reinterpret_cast<float *>(e.out + e.d->out_offset)[e.team * n + tid] = acc;
   }
 };

@@ -316,6 +316,9 @@ __device__ __forceinline__ void pop_top(Stack &s) {
 
 // dst[w] = src[w] ^ key for the words of `bytes` (a multiple of 4), split
 // over `nthr` threads (this one is `idx`); 16-byte vectors when aligned.
+// kBatch keeps four vector loads in flight per thread (16 more registers;
+// off in kernels held to 32 registers).
+template <bool kBatch>
 __device__ __forceinline__ void copy_xor(uint8_t *dst, const uint8_t *src, uint32_t bytes,
                                          uint32_t key, uint32_t idx, uint32_t nthr) {
   uint32_t w0 = 0;
@@ -323,7 +326,22 @@ __device__ __forceinline__ void copy_xor(uint8_t *dst, const uint8_t *src, uint3
     const uint32_t nv = bytes / 16u;
     const uint4 *sv = reinterpret_cast<const uint4 *>(src);
     uint4 *dv = reinterpret_cast<uint4 *>(dst);
-    for (uint32_t i = idx; i < nv; i += nthr) {
+    uint32_t i = idx;
+    // four 16-byte loads in flight before their stores
+    for (; kBatch && i + 3u * nthr < nv; i += 4u * nthr) {
+      uint4 x[4];
+#pragma unroll
+      for (uint32_t u = 0; u < 4u; ++u) x[u] = __ldg(sv + i + u * nthr);
+#pragma unroll
+      for (uint32_t u = 0; u < 4u; ++u) {
+        x[u].x ^= key;
+        x[u].y ^= key;
+        x[u].z ^= key;
+        x[u].w ^= key;
+        dv[i + u * nthr] = x[u];
+      }
+    }
+    for (; i < nv; i += nthr) {
       uint4 x = __ldg(sv + i);
       x.x ^= key;
       x.y ^= key;
@@ -539,7 +557,8 @@ __device__ __forceinline__ void worker_loop(const Env &e0) {
     const uint32_t work = c->work;
     if (work == kTerminate) break;
     if (work == kCopyWork) {
-      copy_xor(c->copy_dst, c->copy_src, c->copy_bytes, c->copy_key, threadIdx.x, W);
+      copy_xor<!P::kDense>(c->copy_dst, c->copy_src, c->copy_bytes, c->copy_key, threadIdx.x,
+                           W);
       named_arrive(kJoinBar, team_threads());
       continue;
     }

@@ -10,7 +10,8 @@ import numpy as np
 
 from . import (TEAM_STATUS_DTYPE, dsr_autotune, dsr_batch_count, dsr_batch_errors,
                dsr_batch_workspace_bytes, dsr_create, dsr_destroy, dsr_launch_batch,
-               dsr_launch_region, dsr_launch_regions, dsr_region_extent, dsr_serve_start,
+               dsr_launch_region, dsr_launch_regions, dsr_region_extent,
+               dsr_region_occupancy, dsr_serve_start,
                dsr_serve_stop, dsr_serve_workspace_bytes, dsr_stack_init, pack_descs)
 
 
@@ -82,6 +83,9 @@ class Runtime:
         if workload.out_dtype == "float32":
             o = o.view(np.float32)
         return o, status.cpu().numpy().view(TEAM_STATUS_DTYPE)
+
+    def occupancy(self, region):
+        return dsr_region_occupancy(self.ctx, region)
 
     @staticmethod
     def extent(region):

@@ -97,3 +97,12 @@ def test_create_without_gpu_fails_cleanly(L):
         dsr.dsr_create(0)
     assert ei.value.code == dsr.DSR_ERR_CUDA
     assert "CUDA" in dsr.dsr_last_error_string(None) or "device" in dsr.dsr_last_error_string(None)
+
+
+def test_occupancy_rejects_missing_context(L):
+    # the occupancy query needs a context with a stack configuration; its
+    # argument checks run before any CUDA call
+    r = wl.nested(teams=8, threads=256, depth=3).regions[0]
+    with pytest.raises(dsr.DsrError) as ei:
+        dsr.dsr_region_occupancy(None, r)
+    assert ei.value.code == dsr.DSR_ERR_INVALID

@@ -188,3 +188,29 @@ def test_hetero_plain_spill(rt):
     g, gs, r, rs = _run_both(rt, work, slab=8192, ovf=3 * 32768, max_teams=512)
     assert np.array_equal(g, r)
     _assert_status_equal(gs, rs)
+
+
+# ---------------------------------------------------------------------------
+# Occupancy of the plain launch, read from the compiled kernel
+# ---------------------------------------------------------------------------
+def test_region_occupancy_matches_model_limits(rt):
+    import paper_1711_10413_gb300 as dsr
+    # nested program, 256 threads: the kernel is held to 32 registers, so
+    # the 64-warp limit (8 CTAs of 8 warps) binds, not registers or smem
+    r = wl.nested(teams=8, threads=256, depth=3).regions[0]
+    _configure(rt, 3264)
+    occ = rt.occupancy(r)
+    assert occ["threads"] == 256 and occ["smem_per_team"] == 384 + 3264
+    assert occ["regs_per_thread"] <= 32 and occ["ctas_per_sm"] == 8
+    assert occ["sm_count"] >= 1 and occ["spill_bytes"] == 0
+    # a 192 KiB sweep frame in the slab leaves room for one CTA per SM
+    s = wl.sweep(196608, teams=2, threads=128).regions[0]
+    _configure(rt, 196608)
+    occ = rt.occupancy(s)
+    assert occ["ctas_per_sm"] == 1 and occ["smem_per_team"] == 384 + 196608
+    model = dsr.dsr_footprint_model(s, 196608, occ["regs_per_thread"])
+    assert model["teams_per_sm"] == occ["ctas_per_sm"] and model["limit"] == 2
+    # the same frame with no slab spills whole to the overflow slab
+    _configure(rt, 0, 196608, 2)
+    occ = rt.occupancy(s)
+    assert occ["spill_bytes"] == 196608 and occ["smem_per_team"] == 384

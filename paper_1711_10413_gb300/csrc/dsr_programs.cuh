@@ -331,7 +331,9 @@ struct ProgNested {
 // ---------------------------------------------------------------------------
 // Config 3: one frame float arr[L] (L = frame_bytes/4) copied from
 // image[team]; out[team*W' + tid] = arr[tid] + arr[tid + W'] + ... in index
-// order, each addition rounded to fp32 (no contraction).
+// order, each addition rounded to fp32 (no contraction). A large frame in
+// the slab is filled by a streamed fill (the region's argument is then 1):
+// the workers sum each chunk as it lands.
 // ---------------------------------------------------------------------------
 struct ProgSweep {
   static constexpr uint32_t kProgram = DSR_PROG_SWEEP;
@@ -342,9 +344,17 @@ struct ProgSweep {
     bool sm;
     uint8_t *f = push(s, S, &sm);
     if (!f) return;
-    fill<!kDense>(s, f, sm, e.images + d.image_offset + static_cast<uint64_t>(e.team) * S, S, 0u);
+    const uint8_t *src = e.images + d.image_offset + static_cast<uint64_t>(e.team) * S;
+    const bool streamed = sm && S >= kStreamMinBytes && fill_streamed(s, f, src, S);
+    if (!streamed) {
+      // a spilled frame's image is pulled towards L2 first, so the copy
+      // across the workers meets fewer DRAM round trips
+      if (!sm && lane_id() == 0) prefetch_l2(src, S & ~15u);
+      fill<!kDense>(s, f, sm, src, S, 0u);
+    }
     if (s.status() != DSR_OK) return;
-    parallel<ProgSweep>(e, 0, region_width(d), 0);
+    parallel<ProgSweep>(e, 0, region_width(d), streamed ? 1u : 0u);
+    stream_finish(s);
     pop(s, f, S);
   }
 
@@ -353,23 +363,32 @@ struct ProgSweep {
     run_threads<ProgSweep>(e, work, first, W, n, arg);
   }
 
-  __device__ static void body(const Env &e, uint32_t, uint32_t tid, uint32_t n, uint32_t) {
+  __device__ static void body(const Env &e, uint32_t, uint32_t tid, uint32_t n,
+                              uint32_t streamed) {
     const float *arr = reinterpret_cast<const float *>(ctrl()->frames[0].ptr);
     const uint32_t L = ctrl()->frames[0].bytes / 4u;
     float acc = 0.0f;
     uint32_t i = tid;
-    // Eight loads in flight, then their additions one by one in index
+    // bytes of a streamed frame known to have landed (all of any other)
+    uint32_t ready = streamed ? 0u : 0xffffffffu;
+    // Sixteen loads in flight, then their additions one by one in index
     // order: the sum is the same left-to-right fp32 sum, but the memory
     // latency (shared memory, or L2/HBM for a spilled frame) is paid once
-    // per eight elements instead of once per element.
-    for (; i + 7u * n < L; i += 8u * n) {
-      float x[8];
+    // per sixteen elements instead of once per element.
+    constexpr uint32_t kB = 16;
+    for (; i + (kB - 1u) * n < L; i += kB * n) {
+      const uint32_t end = 4u * (i + (kB - 1u) * n) + 4u;  // past the batch's last byte
+      if (end > ready) ready = stream_ready(end, ready);
+      float x[kB];
 #pragma unroll
-      for (uint32_t u = 0; u < 8u; ++u) x[u] = arr[i + u * n];
+      for (uint32_t u = 0; u < kB; ++u) x[u] = arr[i + u * n];
 #pragma unroll
-      for (uint32_t u = 0; u < 8u; ++u) acc = __fadd_rn(acc, x[u]);
+      for (uint32_t u = 0; u < kB; ++u) acc = __fadd_rn(acc, x[u]);
     }
-    for (; i < L; i += n) acc = __fadd_rn(acc, arr[i]);
+    for (; i < L; i += n) {
+      if (4u * i + 4u > ready) ready = stream_ready(4u * i + 4u, ready);
+      acc = __fadd_rn(acc, arr[i]);
+    }
     reinterpret_cast<float *>(e.out + e.d->out_offset)[e.team * n + tid] = acc;
   }
 };

@@ -43,6 +43,8 @@ constexpr uint32_t kTerminate = 0xFFFFFFFFu;
 constexpr uint32_t kCopyWork = 0xFFFFFFF0u;  // runtime-internal: workers copy a frame image
 constexpr uint32_t kCtrlBytes = 384;  // control block, slab starts after it
 constexpr uint32_t kParallelCopyBytes = 2048;  // frames filled by the workers from this size
+constexpr uint32_t kStreamChunks = 8;          // mbarriers of a streamed fill
+constexpr uint32_t kStreamMinBytes = 16384;    // slab frames streamed from this size
 
 struct FrameEnt {
   uint8_t *ptr;      // generic address of the frame (shared or global)
@@ -70,6 +72,11 @@ struct __align__(16) Ctrl {
   uint8_t *copy_dst;
   uint32_t copy_bytes;
   uint32_t copy_key;
+  // streamed fill: chunk k of the frame completes on chunk_bar[k]
+  uint64_t chunk_bar[kStreamChunks];
+  uint32_t stream_shift;  // log2 of the chunk size
+  uint16_t stream_phase;  // parity the chunk barriers complete with this fill
+  uint16_t stream_err;    // a worker's wait for a chunk ran out
 };
 static_assert(sizeof(Ctrl) <= kCtrlBytes, "control block too large");
 
@@ -97,6 +104,10 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
                : "memory");
+}
+
+// Makes mbarrier initialisations visible before their first use.
+__device__ __forceinline__ void mbar_init_fence() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
@@ -198,8 +209,9 @@ struct Stack {
   uint32_t hwm;         // peak reserved bytes, slab + overflow
   uint32_t spill;       // peak reserved overflow bytes
   uint32_t bits;        // status (bits 0-7) | fill-mbarrier parity (bit 8) |
-                        // staged copy pending (bit 9) | live depth (bits 12-15) |
-                        // frame k in the slab (bit 16 + k)
+                        // staged copy pending (bit 9) | streamed-fill parity
+                        // (bit 10) | streamed fill pending (bit 11) | live
+                        // depth (bits 12-15) | frame k in the slab (bit 16 + k)
 
   __device__ __forceinline__ int32_t status() const { return static_cast<int32_t>(bits & 0xffu); }
   __device__ __forceinline__ uint32_t phase() const { return (bits >> 8) & 1u; }
@@ -218,9 +230,14 @@ __device__ __forceinline__ void team_setup(Stack &s, uint32_t slab_bytes, uint8_
     c->slab_bytes = slab_bytes;
 #pragma unroll
     for (int k = 0; k < DSR_MAX_DEPTH; ++k) c->chk[k] = 0;
-    if (first) mbar_init(&c->mbar, 1);
+    if (first) {
+      mbar_init(&c->mbar, 1);
+      for (uint32_t k = 0; k < kStreamChunks; ++k) mbar_init(&c->chunk_bar[k], 1);
+      mbar_init_fence();
+    }
   }
-  s.bits = first ? 0u : (s.bits & 0x100u);  // the mbarrier's parity carries over
+  // the mbarriers' parities (fill: bit 8, streamed fill: bit 10) carry over
+  s.bits = first ? 0u : (s.bits & 0x500u);
   s.slab_bytes = slab_bytes;
   s.sp = 0;
   s.gsp = 0;
@@ -504,6 +521,76 @@ __device__ __forceinline__ void key_in_place(uint8_t *dst, uint32_t bytes, uint3
   __syncwarp();
 }
 
+// Streamed fill. A large slab frame's image is copied in up to
+// kStreamChunks power-of-two chunks, chunk k completing on chunk_bar[k],
+// and the master forks right away: the parallel region starts while the
+// image is still arriving, and a worker waits for a chunk only when its
+// reads first reach it (stream_ready). Every element is still read after
+// it has landed, so the region sees the frame the master filled; the
+// copy's latency overlaps the region instead of preceding it. The source
+// must be 16-byte aligned and the size a multiple of 16 (else false: use
+// fill()). stream_finish() (master, after the join) waits for every chunk
+// before the frame may be popped.
+__device__ __forceinline__ bool fill_streamed(Stack &s, uint8_t *dst, const uint8_t *src,
+                                              uint32_t bytes) {
+  if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst) | bytes) & 15u) ||
+      bytes == 0 || (s.bits & 0x800u) || s.status() != DSR_OK)
+    return false;
+  uint32_t shift = 12;
+  while ((kStreamChunks << shift) < bytes) ++shift;
+  if (shift > 15) return false;  // chunks above 32 KiB: not streamed
+  if (lane_id() == 0) {
+    Ctrl *c = ctrl();
+    fence_proxy_async_smem();
+    // every chunk barrier completes one phase per streamed fill (chunks past
+    // the frame's end with no bytes), so one parity serves them all
+    for (uint32_t k = 0; k < kStreamChunks; ++k) {
+      const uint32_t off = k << shift;
+      const uint32_t n = off < bytes ? min(bytes - off, 1u << shift) : 0u;
+      mbar_expect_tx(&c->chunk_bar[k], n);
+      if (n) bulk_g2s(dst + off, src + off, n, &c->chunk_bar[k]);
+    }
+    c->stream_shift = shift;
+    c->stream_phase = static_cast<uint16_t>((s.bits >> 10) & 1u);
+    c->stream_err = 0;
+  }
+  s.bits |= 0x800u;
+  __syncwarp();
+  return true;
+}
+
+// Worker side: make sure bytes [0, byte_end) of the streamed frame have
+// landed, given that [0, ready) are known to have. Returns the new bound
+// (a chunk boundary at or past byte_end). A wait that runs out flags the
+// fill (the master reports TIMEOUT) and goes on.
+__device__ __forceinline__ uint32_t stream_ready(uint32_t byte_end, uint32_t ready) {
+  Ctrl *c = ctrl();
+  const uint32_t shift = c->stream_shift, ph = c->stream_phase;
+  const uint32_t last = (byte_end - 1u) >> shift;
+  for (uint32_t k = ready >> shift; k <= last; ++k)
+    if (!mbar_wait(&c->chunk_bar[k], ph, c->timeout_ns)) c->stream_err = 1;
+  return (last + 1u) << shift;
+}
+
+// Master warp, after the join: wait (bounded) for every chunk of a
+// streamed fill, then flip the parity for the next one.
+__device__ __forceinline__ void stream_finish(Stack &s) {
+  if (!(s.bits & 0x800u)) return;
+  s.bits &= ~0x800u;
+  Ctrl *c = ctrl();
+  const uint32_t ph = (s.bits >> 10) & 1u;
+  bool ok = c->stream_err == 0;
+  for (uint32_t k = 0; k < kStreamChunks; ++k) {
+    if (!mbar_wait(&c->chunk_bar[k], ph, c->timeout_ns)) {
+      mbar_wait(&c->chunk_bar[k], ph, c->timeout_ns);  // copies still in flight
+      ok = false;
+    }
+  }
+  if (!ok) set_status(s, DSR_ERR_TIMEOUT);
+  s.bits ^= 0x400u;
+  __syncwarp();
+}
+
 // Sum of the words [0, words) of a frame (master warp; wrap-around sum, so
 // the lane split gives the same value as one thread summing in order).
 // 16-byte loads when the frame is 16-byte aligned.
@@ -589,6 +676,7 @@ __device__ __forceinline__ void terminate_workers() {
 // Team exit (master warp): unwind what an error left live, then report.
 __device__ __forceinline__ void team_report(const Env &e, Stack &s, dsr_team_status *st) {
   wait_staged(s);  // no bulk copy may still be landing in the slab
+  stream_finish(s);
   const int32_t status = s.status();
   if (status != DSR_OK) {
     while (s.depth()) pop_top(s);

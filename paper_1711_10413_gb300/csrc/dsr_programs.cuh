@@ -197,32 +197,33 @@ struct ProgNested {
           return;
         }
         if (k == 1) {
-          // the staged images land together; key every level's slot now
+          // the staged images land together; key level 1's slot now and
+          // the deeper levels' while level 1's region runs
           wait_staged(s);
-          key_levels(dsr_smem + x0, D, e.team);
+          key_levels(dsr_smem + x0, 0, 1, e.team);
         }
       } else {
         fill<!kDense>(s, f, sm, image(e, k), 1088u, mix32(e.team * 8u + k));
       }
       if (s.status() != DSR_OK) return;
-      if (lane_id() == 0) {
-        uint32_t *w = reinterpret_cast<uint32_t *>(f);
-        if (k > 1) w[0] ^= carry;
-        // the last level's word 15 is final here (its region writes only
-        // the output); earlier levels record their sums below
-        if (k == D) ctrl()->chk[k - 1] = w[15];
-      }
+      uint32_t *w = reinterpret_cast<uint32_t *>(f);
+      if (lane_id() == 0 && k > 1) w[0] ^= carry;
       __syncwarp();
+      // the last level's word 15 is final here (its region writes only the
+      // output); earlier levels record their sums below
+      if (k == D) set_chk(s, k - 1, w[15]);
       uint32_t arg = k;
       if (k < D && sm) arg = kSmemArg | off;
       if (kStaged && k == D) arg = kSmemArg | x0;
-      parallel<ProgNested>(e, k < D ? kUpdate : kInner, region_width(d), arg);
+      fork<ProgNested>(e, k < D ? kUpdate : kInner, region_width(d), arg);
+      // runtime work of the master: key the staged levels 2..D (frames not
+      // pushed yet, slots the running region does not touch)
+      if (kStaged && k == 1 && D > 1) key_levels(dsr_smem + x0, 1, D, e.team);
+      join();
       if (k < D) {
         carry = frame_sum(reinterpret_cast<const uint32_t *>(f) + 16, 256);
-        if (lane_id() == 0) {
-          reinterpret_cast<uint32_t *>(f)[15] = carry;
-          ctrl()->chk[k - 1] = carry;
-        }
+        if (lane_id() == 0) w[15] = carry;
+        set_chk(s, k - 1, carry);
         __syncwarp();
       }
     }
@@ -239,11 +240,11 @@ struct ProgNested {
   }
 
   // XOR level m's slot (1088 bytes from base + 1088 m) with
-  // mix32(team*8 + m + 1), for every level at once (master warp).
-  __device__ static void key_levels(uint8_t *base, uint32_t D, uint32_t team) {
+  // mix32(team*8 + m + 1), for the levels m0 <= m < m1 (master warp).
+  __device__ static void key_levels(uint8_t *base, uint32_t m0, uint32_t m1, uint32_t team) {
     uint4 *v = reinterpret_cast<uint4 *>(base);
-    const uint32_t n = D * 68u;  // 1088 / 16 vectors per level
-    for (uint32_t i = lane_id(); i < n; i += 32u) {
+    const uint32_t n = m1 * 68u;  // 1088 / 16 vectors per level
+    for (uint32_t i = m0 * 68u + lane_id(); i < n; i += 32u) {
       const uint32_t key = mix32(team * 8u + i / 68u + 1u);
       uint4 x = v[i];
       x.x ^= key;
@@ -438,10 +439,10 @@ struct ProgHetero {
       parallel<ProgHetero>(e, k < D ? kUpdate : kInner, width, k);
       if (k < D) {
         c_prev = frame_sum(reinterpret_cast<const uint32_t *>(f), S / 4u);
-        if (lane_id() == 0) ctrl()->chk[k - 1] = c_prev;
+        set_chk(s, k - 1, c_prev);
       }
     }
-    if (lane_id() == 0) ctrl()->chk[D - 1] = frame_words(D - 1)[0];
+    set_chk(s, D - 1, frame_words(D - 1)[0]);
     for (uint32_t k = D; k >= 1; --k) pop(s, ctrl()->frames[k - 1].ptr, d.frame_bytes[k - 1]);
   }
 

@@ -65,7 +65,6 @@ struct __align__(16) Ctrl {
   uint32_t slab_bytes;  // capacity of the shared-memory slab
   uint32_t team;        // batched launch: the current task's team
   uint32_t pad0[2];
-  uint32_t chk[DSR_MAX_DEPTH];
   FrameEnt frames[DSR_MAX_FRAMES];
   dsr_region_desc desc;  // batched launch: the current task's region
   const uint8_t *copy_src;  // kCopyWork arguments
@@ -208,10 +207,12 @@ struct Stack {
   uint32_t gsp;         // overflow-slab bytes reserved
   uint32_t hwm;         // peak reserved bytes, slab + overflow
   uint32_t spill;       // peak reserved overflow bytes
+  uint32_t chk;         // lane k < DSR_MAX_DEPTH: the program's check word k
   uint32_t bits;        // status (bits 0-7) | fill-mbarrier parity (bit 8) |
                         // staged copy pending (bit 9) | streamed-fill parity
                         // (bit 10) | streamed fill pending (bit 11) | live
                         // depth (bits 12-15) | frame k in the slab (bit 16 + k)
+                        // | streamed-fill mbarriers initialised (bit 24)
 
   __device__ __forceinline__ int32_t status() const { return static_cast<int32_t>(bits & 0xffu); }
   __device__ __forceinline__ uint32_t phase() const { return (bits >> 8) & 1u; }
@@ -228,22 +229,27 @@ __device__ __forceinline__ void team_setup(Stack &s, uint32_t slab_bytes, uint8_
     c->ovf_bytes = ovf_bytes;
     c->timeout_ns = timeout_ns;
     c->slab_bytes = slab_bytes;
-#pragma unroll
-    for (int k = 0; k < DSR_MAX_DEPTH; ++k) c->chk[k] = 0;
     if (first) {
       mbar_init(&c->mbar, 1);
-      for (uint32_t k = 0; k < kStreamChunks; ++k) mbar_init(&c->chunk_bar[k], 1);
       mbar_init_fence();
     }
   }
-  // the mbarriers' parities (fill: bit 8, streamed fill: bit 10) carry over
-  s.bits = first ? 0u : (s.bits & 0x500u);
+  // the mbarriers' parities (fill: bit 8, streamed fill: bit 10) and the
+  // streamed fill's set-up flag (bit 24) carry over
+  s.bits = first ? 0u : (s.bits & 0x1000500u);
   s.slab_bytes = slab_bytes;
   s.sp = 0;
   s.gsp = 0;
   s.hwm = 0;
   s.spill = 0;
+  s.chk = 0;
   __syncwarp();
+}
+
+// Record the program's check word k (the same value in every lane): lane k
+// keeps it in a register until the team reports.
+__device__ __forceinline__ void set_chk(Stack &s, uint32_t k, uint32_t v) {
+  if (lane_id() == k) s.chk = v;
 }
 
 __device__ __forceinline__ void set_status(Stack &s, int32_t st) {
@@ -541,6 +547,10 @@ __device__ __forceinline__ bool fill_streamed(Stack &s, uint8_t *dst, const uint
   if (shift > 15) return false;  // chunks above 32 KiB: not streamed
   if (lane_id() == 0) {
     Ctrl *c = ctrl();
+    if (!(s.bits & 0x1000000u)) {  // first streamed fill of this CTA
+      for (uint32_t k = 0; k < kStreamChunks; ++k) mbar_init(&c->chunk_bar[k], 1);
+      mbar_init_fence();
+    }
     fence_proxy_async_smem();
     // every chunk barrier completes one phase per streamed fill (chunks past
     // the frame's end with no bytes), so one parity serves them all
@@ -554,7 +564,7 @@ __device__ __forceinline__ bool fill_streamed(Stack &s, uint8_t *dst, const uint
     c->stream_phase = static_cast<uint16_t>((s.bits >> 10) & 1u);
     c->stream_err = 0;
   }
-  s.bits |= 0x800u;
+  s.bits |= 0x1000800u;
   __syncwarp();
   return true;
 }
@@ -614,9 +624,12 @@ __device__ __forceinline__ uint32_t frame_sum(const uint32_t *f, uint32_t words)
 // Every launch gives a team at least one worker warp: a team declared with
 // no workers (32 threads) runs with one extra warp and a region width of 1,
 // which is the team of one such a region has. The master never runs a body.
+// fork() publishes the work and releases the workers; join() waits for
+// them. parallel() is the two back to back; a master that has runtime work
+// of its own (filling frames it will push later) does it between them.
 template <class P>
-__device__ __forceinline__ void parallel(const Env &e, uint32_t work, uint32_t nthreads,
-                                         uint32_t arg) {
+__device__ __forceinline__ void fork(const Env &e, uint32_t work, uint32_t nthreads,
+                                     uint32_t arg) {
   if (lane_id() == 0) {
     Ctrl *c = ctrl();
     c->work = work;
@@ -624,7 +637,17 @@ __device__ __forceinline__ void parallel(const Env &e, uint32_t work, uint32_t n
     c->arg = arg;
   }
   named_arrive(kForkBar, team_threads());  // release the workers
-  named_bar(kJoinBar, team_threads());     // resume when they are done
+}
+
+__device__ __forceinline__ void join() {
+  named_bar(kJoinBar, team_threads());  // resume when the workers are done
+}
+
+template <class P>
+__device__ __forceinline__ void parallel(const Env &e, uint32_t work, uint32_t nthreads,
+                                         uint32_t arg) {
+  fork<P>(e, work, nthreads, arg);
+  join();
 }
 
 // The worker state machine (Fig. "codegen-worker"): wait for work at the
@@ -682,15 +705,19 @@ __device__ __forceinline__ void team_report(const Env &e, Stack &s, dsr_team_sta
     while (s.depth()) pop_top(s);
   }
   __syncwarp();
+  // the check words come from lanes 0..DSR_MAX_DEPTH-1 (no memory read
+  // after the last join)
+  uint32_t chk[DSR_MAX_DEPTH];
+#pragma unroll
+  for (int k = 0; k < DSR_MAX_DEPTH; ++k) chk[k] = __shfl_sync(0xffffffffu, s.chk, k);
   if (lane_id() == 0) {
-    const Ctrl *c = ctrl();
     dsr_team_status r;
     r.status = status;
     r.depth_final = s.depth();
     r.hwm_bytes = s.hwm;
     r.spill_bytes = s.spill;
 #pragma unroll
-    for (int k = 0; k < DSR_MAX_DEPTH; ++k) r.chk[k] = status == DSR_OK ? c->chk[k] : 0u;
+    for (int k = 0; k < DSR_MAX_DEPTH; ++k) r.chk[k] = status == DSR_OK ? chk[k] : 0u;
     st[e.d->status_index + e.team] = r;
   }
 }

@@ -210,7 +210,7 @@ def hetero_stack_bytes(regions) -> int:
     return total
 
 
-def measure_sweep(dsr, torch, device, flush, hbm_gbs):
+def measure_sweep(dsr, torch, device, flush, hbm_gbs, sizes=None):
     """Config 3: one fp32 frame per team, 512 teams x 128 threads, for each
     frame size placed in the shared-memory slab (when one CTA can hold it)
     and in the global overflow slab; HBM bytes per launch = images read +
@@ -219,7 +219,7 @@ def measure_sweep(dsr, torch, device, flush, hbm_gbs):
     rt = dsr.Runtime(device, slab_bytes=0, overflow_bytes_per_team=max(wl.SWEEP_SIZES),
                      max_teams=teams)
     res = []
-    for S in wl.SWEEP_SIZES:
+    for S in sizes or wl.SWEEP_SIZES:
         work = wl.sweep(S, teams=teams, threads=threads)
         region = work.regions[0]
         images, out, status = rt.device_buffers(work)
@@ -249,11 +249,28 @@ def measure_sweep(dsr, torch, device, flush, hbm_gbs):
     return dict(workload="sweep_512x128", teams=teams, threads=threads, runs=res)
 
 
-def measure_forms(dsr, torch, device, flush, hbm_gbs):
+FORMS = ("sweep", "scalars", "batched", "served")
+
+
+def measure_forms(dsr, torch, device, flush, hbm_gbs, which=FORMS, instances=10000,
+                  sweep_sizes=None):
     forms = {}
     sm_count = torch.cuda.get_device_properties(device).multi_processor_count
-    forms["sweep"] = measure_sweep(dsr, torch, device, flush, hbm_gbs)
+    if "sweep" in which:
+        forms["sweep"] = measure_sweep(dsr, torch, device, flush, hbm_gbs, sweep_sizes)
     rt = dsr.Runtime(device, slab_bytes=16384, overflow_bytes_per_team=3 * 32768, max_teams=4096)
+    if "scalars" in which:
+        forms.update(measure_scalars(dsr, torch, rt, flush))
+    if "batched" in which:
+        forms.update(measure_batched(dsr, torch, rt, flush, sm_count, instances))
+    if "served" in which:
+        forms.update(measure_served(dsr, rt))
+    rt.close()
+    return forms
+
+
+def measure_scalars(dsr, torch, rt, flush):
+    forms = {}
     # config 1: 1000 sequential regions of one team
     sc = wl.scalars(n_regions=1000, teams=1, threads=128)
     one = wl.scalars(n_regions=1, teams=1, threads=128)
@@ -270,9 +287,14 @@ def measure_forms(dsr, torch, device, flush, hbm_gbs):
                             one_launch_regions_per_s=1000 / (ms_all * 1e-3),
                             per_launch_regions_per_s=1000 / (ms_each * 1e-3),
                             handoff_ns_per_region=ms_all * 1e6 / 1000)
+    return forms
+
+
+def measure_batched(dsr, torch, rt, flush, sm_count, instances=10000):
+    forms = {}
     # config 4: batched vs per-launch
     rt.configure(16384, 3 * 32768, 4096)
-    work = wl.hetero(n_instances=10000)
+    work = wl.hetero(n_instances=instances)
     b = rt.batch_buffers(work)
     tuning, _ = rt.autotune(b)
     ms_batch = _event_ms(torch, lambda: rt.launch_batch(b, tuning, use_graph=True), 5, flush)
@@ -281,9 +303,10 @@ def measure_forms(dsr, torch, device, flush, hbm_gbs):
     st = b["status"].cpu().numpy().view(dsr.TEAM_STATUS_DTYPE)
     stack = hetero_stack_bytes(work.regions)
     smem_gbs = stack / (ms_batch * 1e-3) / 1e9
-    forms["batched"] = dict(workload="hetero_10000_instances", instances=10000, teams=counted,
-                            tuning=tuning, batched_regions_per_s=10000 / (ms_batch * 1e-3),
-                            per_launch_regions_per_s=10000 / (ms_plain * 1e-3),
+    forms["batched"] = dict(workload="hetero_%d_instances" % instances, instances=instances,
+                            teams=counted, tuning=tuning,
+                            batched_regions_per_s=instances / (ms_batch * 1e-3),
+                            per_launch_regions_per_s=instances / (ms_plain * 1e-3),
                             batched_push_pop_per_s=sum(r.teams * r.depth for r in work.regions)
                             / (ms_batch * 1e-3),
                             speedup=ms_plain / ms_batch,
@@ -296,6 +319,11 @@ def measure_forms(dsr, torch, device, flush, hbm_gbs):
                             device_rejects=err,
                             bad_team_status=int((st["status"] != 0).sum()))
     del b
+    return forms
+
+
+def measure_served(dsr, rt):
+    forms = {}
     # config 5: served at several rates vs per-request launches. 100,000
     # requests per rate cycle over 20,000 distinct instances (a request's
     # twins rewrite the same output rows with the same values); the first
@@ -337,7 +365,6 @@ def measure_forms(dsr, torch, device, flush, hbm_gbs):
     forms["served"] = dict(workload="hetero_poisson_%d_requests_%d_distinct" % (n, distinct),
                            warmup_dropped=warm, overflow_pool_bytes=pool_per_cta * pool_ctas,
                            server=served, per_request_launch=launched)
-    rt.close()
     return forms
 
 
@@ -353,7 +380,12 @@ def main():
     ap.add_argument("--workload", default="nested")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--forms", default="all", choices=["all", "none"])
+    ap.add_argument("--forms", default="all",
+                    help="all, none, or a comma-separated list of " + ", ".join(FORMS))
+    ap.add_argument("--instances", type=int, default=10000,
+                    help="instances of the batched form")
+    ap.add_argument("--sweep-sizes", default="",
+                    help="comma-separated frame sizes of the sweep form (default: all six)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -492,8 +524,12 @@ def main():
         bad_team_status=bad_status,
         clocks=clk,
     )
-    if world == 1 and args.forms == "all":
-        line["forms"] = measure_forms(dsr, torch, local, flush, peaks["hbm_gbs"])
+    which = FORMS if args.forms == "all" else [f for f in args.forms.split(",")
+                                               if f and f != "none"]
+    if world == 1 and which:
+        sizes = [int(x) for x in args.sweep_sizes.split(",") if x]
+        line["forms"] = measure_forms(dsr, torch, local, flush, peaks["hbm_gbs"], which,
+                                      args.instances, sizes or None)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = time_oracle(work, slab, ovf, budget_s=args.cpu_budget)
     print(json.dumps(line))

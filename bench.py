@@ -54,7 +54,7 @@ SERVE_SHAPES = [dict(threads=256, slab_bytes=16384), dict(threads=128, slab_byte
 # DRAM traffic (read + write bytes per launch) of the plain nested kernel from
 # one ncu capture (profiles/nested_1024x256_d3_full.md), keyed by a hash of
 # the sources that kernel is built from; any change to them makes it null.
-TRAFFIC_BY_SOURCE = {"39e22b884abd7bac": 3385088}
+TRAFFIC_BY_SOURCE = {"8dc4a752c77e6fea": 3392768}
 KERNEL_SOURCES = ["paper_1711_10413_gb300/csrc/dsr_runtime.cuh",
                   "paper_1711_10413_gb300/csrc/dsr_programs.cuh",
                   "paper_1711_10413_gb300/csrc/dsr_check.cuh",
@@ -253,7 +253,7 @@ FORMS = ("sweep", "scalars", "batched", "served")
 
 
 def measure_forms(dsr, torch, device, flush, hbm_gbs, which=FORMS, instances=10000,
-                  sweep_sizes=None):
+                  sweep_sizes=None, tuning=None):
     forms = {}
     sm_count = torch.cuda.get_device_properties(device).multi_processor_count
     if "sweep" in which:
@@ -262,7 +262,7 @@ def measure_forms(dsr, torch, device, flush, hbm_gbs, which=FORMS, instances=100
     if "scalars" in which:
         forms.update(measure_scalars(dsr, torch, rt, flush))
     if "batched" in which:
-        forms.update(measure_batched(dsr, torch, rt, flush, sm_count, instances))
+        forms.update(measure_batched(dsr, torch, rt, flush, sm_count, instances, tuning))
     if "served" in which:
         forms.update(measure_served(dsr, rt))
     rt.close()
@@ -290,13 +290,14 @@ def measure_scalars(dsr, torch, rt, flush):
     return forms
 
 
-def measure_batched(dsr, torch, rt, flush, sm_count, instances=10000):
+def measure_batched(dsr, torch, rt, flush, sm_count, instances=10000, tuning=None):
     forms = {}
     # config 4: batched vs per-launch
     rt.configure(16384, 3 * 32768, 4096)
     work = wl.hetero(n_instances=instances)
     b = rt.batch_buffers(work)
-    tuning, _ = rt.autotune(b)
+    if tuning is None:
+        tuning, _ = rt.autotune(b)
     ms_batch = _event_ms(torch, lambda: rt.launch_batch(b, tuning, use_graph=True), 5, flush)
     err, counted = rt.batch_errors(b)
     ms_plain = _event_ms(torch, lambda: rt.launch_regions(b), 2, flush)
@@ -384,6 +385,8 @@ def main():
                     help="all, none, or a comma-separated list of " + ", ".join(FORMS))
     ap.add_argument("--instances", type=int, default=10000,
                     help="instances of the batched form")
+    ap.add_argument("--tuning", default="",
+                    help="threads,slab_bytes of the batched form (default: autotuned)")
     ap.add_argument("--sweep-sizes", default="",
                     help="comma-separated frame sizes of the sweep form (default: all six)")
     args = ap.parse_args()
@@ -528,8 +531,12 @@ def main():
                                                if f and f != "none"]
     if world == 1 and which:
         sizes = [int(x) for x in args.sweep_sizes.split(",") if x]
+        tuning = None
+        if args.tuning:
+            th, sl = (int(x) for x in args.tuning.split(","))
+            tuning = dict(threads=th, slab_bytes=sl, ctas_per_sm=0)
         line["forms"] = measure_forms(dsr, torch, local, flush, peaks["hbm_gbs"], which,
-                                      args.instances, sizes or None)
+                                      args.instances, sizes or None, tuning)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = time_oracle(work, slab, ovf, budget_s=args.cpu_budget)
     print(json.dumps(line))

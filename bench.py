@@ -19,7 +19,11 @@ The same JSON line also carries the other configurations and launch forms
   served   - the same instance distribution submitted open-loop (Poisson)
              to the device-resident server at several rates: p50/p99
              latency and sustained requests/s, against one plain launch per
-             request under the same arrivals.
+             request under the same arrivals;
+  workers  - worker-level sharing, 1024 teams x 256 threads: every worker
+             pushes a 256-byte frame on its warp's stack for a nested region
+             on its warp, with the warp stacks in the slab and on the global
+             stack.
 
 Prints ONE JSON line (rank 0). `--impl reference` times the CPU oracle on
 the same workload instead.
@@ -249,7 +253,40 @@ def measure_sweep(dsr, torch, device, flush, hbm_gbs, sizes=None):
     return dict(workload="sweep_512x128", teams=teams, threads=threads, runs=res)
 
 
-FORMS = ("sweep", "scalars", "batched", "served")
+FORMS = ("sweep", "scalars", "batched", "served", "workers")
+
+
+def measure_workers(dsr, torch, device, flush, sm_count):
+    """Worker-level sharing: 1024 teams x 256 threads, each of the 224
+    workers pushes a 256-byte frame on its warp's stack and runs a nested
+    region on its warp. Warp stacks in the slab, then all on the global
+    (overflow) stack. Stack bytes per worker frame: written by the fill,
+    read and written by the nested region, read by the worker's sum."""
+    teams, threads, S = 1024, 256, 256
+    W = threads - 32
+    work = wl.workers(teams=teams, threads=threads, frame_bytes=S)
+    region = work.regions[0]
+    rt = dsr.Runtime(device, slab_bytes=0, overflow_bytes_per_team=16 + W * S, max_teams=teams)
+    images, out, status = rt.device_buffers(work)
+    stack = teams * W * 4 * S
+    runs = []
+    for where, slab, ovf in (("slab", 16 + W * S, 0), ("overflow", 16, W * S)):
+        rt.configure(slab, ovf, teams if ovf else 0)
+        occ = rt.occupancy(region)
+        ms = _event_ms(torch, lambda: dsr.dsr_launch_region(rt.ctx, region, images, out, status),
+                       10, flush)
+        st = status.cpu().numpy().view(dsr.TEAM_STATUS_DTYPE)
+        gbs = stack / (ms * 1e-3) / 1e9
+        runs.append(dict(placement=where, us=ms * 1e3, regions_per_s=1.0 / (ms * 1e-3),
+                         worker_frames_per_s=teams * W / (ms * 1e-3), stack_bytes=stack,
+                         stack_gbs=gbs, smem_frac=gbs / smem_peak_gbs(sm_count),
+                         smem_per_team=occ["smem_per_team"], ctas_per_sm=occ["ctas_per_sm"],
+                         regs_per_thread=occ["regs_per_thread"],
+                         spill_bytes_per_team=int(st["spill_bytes"].max()),
+                         bad_team_status=int((st["status"] != 0).sum())))
+    rt.close()
+    return dict(workload="workers_1024x256_256B", teams=teams, threads=threads,
+                worker_frame_bytes=S, runs=runs)
 
 
 def measure_forms(dsr, torch, device, flush, hbm_gbs, which=FORMS, instances=10000,
@@ -266,6 +303,8 @@ def measure_forms(dsr, torch, device, flush, hbm_gbs, which=FORMS, instances=100
     if "served" in which:
         forms.update(measure_served(dsr, rt))
     rt.close()
+    if "workers" in which:
+        forms["workers"] = measure_workers(dsr, torch, device, flush, sm_count)
     return forms
 
 

@@ -81,7 +81,19 @@ enum {
   /* heterogeneous instances: depth levels of int32[frame_bytes[k]/4] from
    * per-instance images; innermost out[team*width + tid] = hash-sum of the
    * worker's strided elements of every live frame. */
-  DSR_PROG_HETERO = 6
+  DSR_PROG_HETERO = 6,
+  /* sharing at worker level (Sec. 7, future work: the all-to-all pattern
+   * and a runtime-managed global stack): depth 2, frame_bytes = {16, S},
+   * threads >= 64. The master pushes int32 s[4] from the team's image; in
+   * the parallel region every worker t < width pushes its own frame G_t =
+   * int32[S/4] (image words ^ mix32(s0 + t)) on a stack of its warp, and
+   * runs a nested parallel region on its warp's 32 lanes, which get the
+   * frame's address by shuffle: G_t[w] = mix32(G_t[w] + s1 + w); then
+   * out[team*width + t] = (sum G_t) ^ s2. The warp stacks share out what
+   * the team's slab and overflow slab have left, evenly over the W/32
+   * worker warps; a worker frame that fits neither share gives OVERFLOW.
+   * chk[0] = sum of the team's outputs. Plain launch only. */
+  DSR_PROG_WORKERS = 7
 };
 
 /* One region instance: a target region with `teams` teams (one CTA each in

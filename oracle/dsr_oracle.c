@@ -53,6 +53,7 @@
 
 #define ORC_MAX_LEVELS 4   /* frame sizes a region descriptor carries */
 #define ORC_STACK_CAP 16   /* frame-table entries per team */
+#define ORC_WARP_CAP 32    /* frames of one warp's stack (one per lane) */
 
 enum {
   PROG_PAPER_SCALARS = 1,
@@ -61,6 +62,7 @@ enum {
   PROG_NESTED = 4,
   PROG_SWEEP = 5,
   PROG_HETERO = 6,
+  PROG_WORKERS = 7,
 };
 
 /* One region instance (64 bytes). */
@@ -110,7 +112,8 @@ typedef struct {
 } orc_frame;
 
 typedef struct {
-  orc_frame f[ORC_STACK_CAP];
+  orc_frame f[ORC_WARP_CAP];
+  uint32_t cap; /* frame-table entries: ORC_STACK_CAP, or ORC_WARP_CAP for a warp's stack */
   uint32_t depth;
   uint64_t slab_cap, ovf_cap;
   uint64_t slab_used, ovf_used;
@@ -120,6 +123,7 @@ typedef struct {
 
 static void stack_init(orc_stack *s, uint64_t slab_cap, uint64_t ovf_cap) {
   memset(s, 0, sizeof(*s));
+  s->cap = ORC_STACK_CAP;
   s->slab_cap = slab_cap;
   s->ovf_cap = ovf_cap;
 }
@@ -127,7 +131,7 @@ static void stack_init(orc_stack *s, uint64_t slab_cap, uint64_t ovf_cap) {
 static uint8_t *push(orc_stack *s, uint32_t bytes) {
   uint64_t fp = ((uint64_t)bytes + 15u) & ~(uint64_t)15u;
   int in_slab;
-  if (s->depth == ORC_STACK_CAP) {
+  if (s->depth == s->cap) {
     s->status = ORC_ERR_OVERFLOW;
     return NULL;
   }
@@ -390,6 +394,81 @@ static void team_hetero(const orc_region *d, uint32_t team, const uint8_t *img,
 }
 
 /* ------------------------------------------------------------------------ */
+/* P5 "workers": sharing at worker level, the all-to-all pattern the paper  */
+/* leaves to future work (Sec. 7), with each worker's frame on a stack of   */
+/* its warp and the runtime-managed global stack behind it (Sec. 7); the    */
+/* nested team of a worker is its warp's 32 lanes (the CUDA-NP mapping of   */
+/* Sec. 2: a warp's other threads run the nested parallel region).          */
+/* Image of team t at image_offset + t * (16 + pad16(S)): int32 s[4], then   */
+/* int32 base[L], L = S/4, S = frame_bytes[1].                               */
+/*   master: push F = s[4] (frame_bytes[0] = 16) from the image.            */
+/*   outer parallel, width W': outer thread t = 0 .. W'-1:                   */
+/*     push G_t = int32[L] on the stack of warp t/32;                        */
+/*     G_t[i] = base[i] ^ mix32(F.s0 + t);                                   */
+/*     nested parallel, 32 threads j: for w = j; w < L; w += 32:             */
+/*       G_t[w] = mix32(G_t[w] + F.s1 + w);                                  */
+/*     out[team*W' + t] = (sum_w G_t[w]) ^ F.s2.                             */
+/*   A warp's outer threads push in lane order, all before any of their     */
+/*   nested regions, and pop in reverse order.                               */
+/*   master after the join: chk[0] = sum_{t < W'} out[team*W' + t]; pop F.   */
+/* Warp stacks: what the team's slab and overflow slab have left after F is */
+/* split evenly, in 16-byte units, over the W/32 worker warps; a warp's     */
+/* stack places each frame first fit (its slab share, else its overflow     */
+/* share). A push that fits neither makes the team OVERFLOW, and that outer */
+/* thread runs nothing. hwm and spill add the team stack's peaks and every  */
+/* warp stack's peaks.                                                      */
+/* ------------------------------------------------------------------------ */
+static void team_workers(const orc_region *d, uint32_t team, const uint8_t *img,
+                         uint8_t *out, orc_stack *s, orc_team_status *st) {
+  uint32_t Wp = width(d), L = d->frame_bytes[1] / 4;
+  uint32_t nwarps = team_width(d) / 32;
+  uint64_t stride = 16u + (((uint64_t)d->frame_bytes[1] + 15u) & ~(uint64_t)15u);
+  const uint8_t *timg = img + d->image_offset + (uint64_t)team * stride;
+  uint32_t *o = (uint32_t *)(out + d->out_offset);
+  uint8_t *F = push(s, 16);
+  if (!F) return;
+  memcpy(F, timg, 16);
+  uint64_t wslab = ((s->slab_cap - s->slab_used) / nwarps) & ~(uint64_t)15u;
+  uint64_t wovf = ((s->ovf_cap - s->ovf_used) / nwarps) & ~(uint64_t)15u;
+  uint64_t whwm = 0, wspill = 0;
+  int failed = 0;
+  for (uint32_t w = 0; w < nwarps; w++) {
+    orc_stack ws;
+    stack_init(&ws, wslab, wovf);
+    ws.cap = ORC_WARP_CAP;
+    uint8_t *G[32] = {0};
+    uint32_t lanes = 0; /* outer threads of this warp */
+    while (lanes < 32 && w * 32 + lanes < Wp) lanes++;
+    for (uint32_t l = 0; l < lanes; l++) { /* pushes, in lane order */
+      G[l] = push(&ws, d->frame_bytes[1]);
+      if (!G[l]) break;
+      uint32_t t = w * 32 + l, key = orc_mix32(ld32(F) + t);
+      for (uint32_t i = 0; i < L; i++) st32(G[l] + 4 * i, ld32(timg + 16 + 4ull * i) ^ key);
+    }
+    for (uint32_t l = 0; l < lanes && G[l]; l++) { /* nested regions, then results */
+      uint32_t t = w * 32 + l;
+      for (uint32_t j = 0; j < 32; j++)
+        for (uint32_t i = j; i < L; i += 32)
+          st32(G[l] + 4 * i, orc_mix32(ld32(G[l] + 4 * i) + ld32(F + 4) + i));
+      uint32_t sum = 0;
+      for (uint32_t i = 0; i < L; i++) sum += ld32(G[l] + 4 * i);
+      o[(uint64_t)team * Wp + t] = sum ^ ld32(F + 8);
+    }
+    if (ws.status != ORC_OK) failed = 1;
+    whwm += ws.hwm;
+    wspill += ws.spill_hwm;
+    unwind(&ws); /* pops in reverse push order */
+  }
+  if (failed) s->status = ORC_ERR_OVERFLOW;
+  s->hwm += whwm;
+  s->spill_hwm += wspill;
+  uint32_t c = 0;
+  for (uint32_t t = 0; t < Wp; t++) c += o[(uint64_t)team * Wp + t];
+  st->chk[0] = c;
+  pop(s, F);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Descriptor checks: the sizes each program's frames must have.           */
 /* ------------------------------------------------------------------------ */
 static int check_region(const orc_region *d) {
@@ -415,6 +494,8 @@ static int check_region(const orc_region *d) {
       return d->depth == 1;
     case PROG_HETERO:
       return 1;
+    case PROG_WORKERS:
+      return d->depth == 2 && d->frame_bytes[0] == 16 && d->threads >= 64;
     default:
       return 0;
   }
@@ -446,6 +527,7 @@ int orc_run(const orc_region *d, const uint8_t *images, uint8_t *out, orc_team_s
       case PROG_NESTED: team_nested(d, team, images, out, &s, &st); break;
       case PROG_SWEEP: team_sweep(d, team, images, out, &s); break;
       case PROG_HETERO: team_hetero(d, team, images, out, &s, &st); break;
+      case PROG_WORKERS: team_workers(d, team, images, out, &s, &st); break;
     }
     if (s.status != ORC_OK) memset(st.chk, 0, sizeof(st.chk));
     unwind(&s); /* no-op for a program that popped everything */

@@ -31,6 +31,7 @@ DSR_PROG_SCALARS = 3
 DSR_PROG_NESTED = 4
 DSR_PROG_SWEEP = 5
 DSR_PROG_HETERO = 6
+DSR_PROG_WORKERS = 7
 
 
 class dsr_region_desc(ctypes.Structure):

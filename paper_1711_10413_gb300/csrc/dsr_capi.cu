@@ -70,6 +70,7 @@ KernelFn plain_kernel_for(uint32_t program, uint32_t threads) {
     case DSR_PROG_NESTED: return pick<ProgNested>(threads);
     case DSR_PROG_SWEEP: return pick<ProgSweep>(threads);
     case DSR_PROG_HETERO: return pick<ProgHetero>(threads);
+    case DSR_PROG_WORKERS: return pick<ProgWorkers>(threads);
     default: return nullptr;
   }
 }
@@ -245,7 +246,7 @@ extern "C" int32_t dsr_destroy(dsr_ctx *ctx) {
 
 static int32_t set_smem_attr(dsr_ctx *ctx, uint32_t smem) {
   static const uint32_t kThreads[] = {128, 256, 512, 1024};
-  for (uint32_t p = DSR_PROG_PAPER_SCALARS; p <= DSR_PROG_HETERO; ++p)
+  for (uint32_t p = DSR_PROG_PAPER_SCALARS; p <= DSR_PROG_WORKERS; ++p)
     for (uint32_t t : kThreads) {
       const void *k = reinterpret_cast<const void *>(plain_kernel_for(p, t));
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -55,6 +55,8 @@ DSR_HD int shape_error(const dsr_region_desc &d) {
       return d.depth != 1 ? 4 : 0;
     case DSR_PROG_HETERO:
       return 0;
+    case DSR_PROG_WORKERS:
+      return (d.depth != 2 || d.frame_bytes[0] != 16 || d.threads < 64) ? 4 : 0;
     default:
       return 5;
   }
@@ -75,6 +77,7 @@ DSR_HD void extent(const dsr_region_desc &d, uint64_t *ib, uint64_t *ob, uint64_
       for (uint32_t k = 0; k < d.depth; ++k) i += pad16(d.frame_bytes[k]);
       o = 4 * T * w;
       break;
+    case DSR_PROG_WORKERS: i = T * (16u + pad16(d.frame_bytes[1])); o = 4 * T * w; break;
   }
   *ib = i;
   *ob = o;

@@ -503,4 +503,132 @@ struct ProgHetero {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Worker-level sharing (Sec. 7, future work: sharing among workers, an
+// all-to-all pattern that needs far more stack, with a runtime-managed
+// global stack behind the shared one). The master pushes F = int32 s[4]
+// from the team's image and forks. Every worker t < W' is then itself the
+// master of a nested parallel region: it pushes G_t = int32[L] on a stack
+// of its own warp, G_t[i] = base[i] ^ mix32(s0 + t), and its nested team
+// -- the 32 lanes of its warp, the mapping of CUDA-NP (Sec. 2) -- runs
+// G_t[w] = mix32(G_t[w] + s1 + w); afterwards out[team*W' + t] =
+// (sum G_t) ^ s2. After the join the master stores chk[0] = sum of the
+// team's outputs and pops F.
+//
+// Warp stacks. What the team's slab and overflow slab have left after F is
+// split evenly (16-byte units) over the W/32 worker warps. A warp pushes
+// its lanes' frames in lane order, first fit (its slab share, else its
+// overflow share); a frame that fits neither makes the team OVERFLOW and
+// that worker (and the warp's later ones, whose frames fit no better) runs
+// nothing. The frames stay live until the warp's last nested region has
+// run, then are popped in reverse order. The stack pointers never leave
+// registers: every frame has the same size, so lane l's slot follows from
+// l. A frame's address reaches the nested team by a warp shuffle (the
+// frame table of the warp is a register per lane).
+// ---------------------------------------------------------------------------
+struct ProgWorkers {
+  static constexpr uint32_t kProgram = DSR_PROG_WORKERS;
+  static constexpr bool kDense = false;
+
+  __device__ static const uint8_t *image(const Env &e) {
+    const dsr_region_desc &d = *e.d;
+    return e.images + d.image_offset +
+           static_cast<uint64_t>(e.team) * (16u + ((d.frame_bytes[1] + 15u) & ~15u));
+  }
+
+  __device__ static void master(const Env &e, Stack &s) {
+    const dsr_region_desc &d = *e.d;
+    uint8_t *F = push(s, 16);
+    if (!F) return;
+    if (lane_id() == 0)
+      *reinterpret_cast<uint4 *>(F) = __ldg(reinterpret_cast<const uint4 *>(image(e)));
+    // the warp stacks' shares of what the team's stack has left
+    const uint32_t nwarps = team_workers() / 32u;
+    const uint64_t ovf_left = ctrl()->ovf_bytes - s.gsp;
+    if (lane_id() == 0) {
+      Ctrl *c = ctrl();
+      c->wstack_off = kCtrlBytes + s.sp;
+      c->wslab = ((s.slab_bytes - s.sp) / nwarps) & ~15u;
+      c->wovf = c->ovf ? c->ovf + s.gsp : nullptr;
+      c->wovf_bytes = c->ovf ? (ovf_left / nwarps) & ~15ull : 0ull;
+      c->whwm = 0;
+      c->wspill = 0;
+      c->wfail = 0;
+    }
+    __syncwarp();
+    const uint32_t width = region_width(d);
+    parallel<ProgWorkers>(e, 0, width, 0);
+    const Ctrl *c = ctrl();
+    s.hwm += c->whwm;
+    s.spill += c->wspill;
+    if (c->wfail) set_status(s, DSR_ERR_OVERFLOW);
+    // the workers' outputs, read by the master after the join
+    const uint32_t *o = reinterpret_cast<const uint32_t *>(e.out + d.out_offset) +
+                        static_cast<uint64_t>(e.team) * width;
+    uint32_t v = 0;
+    for (uint32_t t = lane_id(); t < width; t += 32u) v += o[t];
+    set_chk(s, 0, warp_sum(v));
+    pop(s, F, 16);
+  }
+
+  // Every worker thread calls run() once (the region is no wider than the
+  // workers); the warp is the unit of work.
+  __device__ static void run(const Env &e, uint32_t, uint32_t tid, uint32_t, uint32_t n,
+                             uint32_t) {
+    const uint32_t lane = lane_id(), warp = tid >> 5, t0 = warp << 5;
+    if (t0 >= n) return;  // no worker of this warp takes part (uniform in the warp)
+    const uint32_t lanes = min(32u, n - t0);  // workers t0 .. t0 + lanes - 1
+    Ctrl *c = ctrl();
+    const dsr_region_desc &d = *e.d;
+    const uint32_t L = d.frame_bytes[1] / 4u;
+    const uint32_t fp = (d.frame_bytes[1] + 15u) & ~15u;
+    // this warp's stack: lane order, first fit into the slab share, then
+    // the overflow share
+    const uint32_t in_slab = min(lanes, c->wslab / fp);
+    const uint64_t ovf_fit = c->wovf_bytes / fp;
+    const uint32_t pushed =
+        static_cast<uint32_t>(min(static_cast<uint64_t>(lanes), in_slab + ovf_fit));
+    uint8_t *mine = nullptr;
+    if (lane < pushed)
+      mine = lane < in_slab ? dsr_smem + c->wstack_off + warp * c->wslab + lane * fp
+                            : c->wovf + warp * c->wovf_bytes + static_cast<uint64_t>(lane - in_slab) * fp;
+    if (lane == 0) {
+      atomicAdd(&c->whwm, pushed * fp);
+      atomicAdd(&c->wspill, (pushed - min(pushed, in_slab)) * fp);
+      if (pushed < lanes) atomicOr(&c->wfail, 1u);
+    }
+    const uint32_t *F = reinterpret_cast<const uint32_t *>(c->frames[0].ptr);
+    const uint32_t s0 = F[0], s1 = F[1], s2 = F[2];
+    const uint32_t *base = reinterpret_cast<const uint32_t *>(image(e) + 16);
+    const uintptr_t my = reinterpret_cast<uintptr_t>(mine);
+    // each worker's sequential part: fill its frame (order-free word copy,
+    // done by the warp's lanes)
+    for (uint32_t l = 0; l < pushed; ++l) {
+      uint32_t *g = reinterpret_cast<uint32_t *>(__shfl_sync(0xffffffffu, my, l));
+      const uint32_t key = mix32(s0 + t0 + l);
+      for (uint32_t i = lane; i < L; i += 32u) g[i] = __ldg(base + i) ^ key;
+    }
+    __syncwarp();
+    uint32_t result = 0;
+    for (uint32_t l = 0; l < pushed; ++l) {
+      // fork of worker t0 + l's nested region: its frame address, by shuffle
+      uint32_t *g = reinterpret_cast<uint32_t *>(__shfl_sync(0xffffffffu, my, l));
+      for (uint32_t w = lane; w < L; w += 32u) g[w] = mix32(g[w] + s1 + w);
+      __syncwarp();  // join
+      // the worker's sum of its frame (wrap-around, order-free: the warp's lanes)
+      uint32_t part = 0;
+      for (uint32_t w = lane; w < L; w += 32u) part += g[w];
+      const uint32_t sum = warp_sum(part);
+      if (lane == l) result = sum ^ s2;
+    }
+    if (lane < pushed)
+      reinterpret_cast<uint32_t *>(e.out + d.out_offset)[static_cast<uint64_t>(e.team) * n + t0 +
+                                                          lane] = result;
+    // the warp's frames are popped in reverse order: with register stack
+    // pointers that is the end of the region
+  }
+
+  __device__ static void body(const Env &, uint32_t, uint32_t, uint32_t, uint32_t) {}
+};
+
 }  // namespace dsr

@@ -64,7 +64,8 @@ struct __align__(16) Ctrl {
   uint64_t ovf_bytes;
   uint32_t slab_bytes;  // capacity of the shared-memory slab
   uint32_t team;        // batched launch: the current task's team
-  uint32_t pad0[2];
+  uint32_t whwm;    // worker-level stacks: sum of the warp stacks' peak bytes
+  uint32_t wspill;  // ... and of their peak overflow bytes
   FrameEnt frames[DSR_MAX_FRAMES];
   dsr_region_desc desc;  // batched launch: the current task's region
   const uint8_t *copy_src;  // kCopyWork arguments
@@ -76,6 +77,13 @@ struct __align__(16) Ctrl {
   uint32_t stream_shift;  // log2 of the chunk size
   uint16_t stream_phase;  // parity the chunk barriers complete with this fill
   uint16_t stream_err;    // a worker's wait for a chunk ran out
+  // worker-level stacks: each worker warp's share of what the team's slab
+  // and overflow slab have left (set by the master before the fork)
+  uint32_t wstack_off;   // shared-memory offset of warp 0's slab share
+  uint32_t wslab;        // slab bytes per warp (a multiple of 16)
+  uint8_t *wovf;         // warp 0's overflow share
+  uint64_t wovf_bytes;   // overflow bytes per warp (a multiple of 16)
+  uint32_t wfail;        // a worker frame fitted neither share
 };
 static_assert(sizeof(Ctrl) <= kCtrlBytes, "control block too large");
 

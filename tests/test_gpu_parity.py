@@ -214,3 +214,61 @@ def test_region_occupancy_matches_model_limits(rt):
     _configure(rt, 0, 196608, 2)
     occ = rt.occupancy(s)
     assert occ["spill_bytes"] == 196608 and occ["smem_per_team"] == 384
+
+
+# ---------------------------------------------------------------------------
+# Worker-level sharing (Sec. 7): per-warp stacks, nested regions on warps
+# ---------------------------------------------------------------------------
+def _same_out(g, r):
+    """The device output buffer is padded to 16 bytes; the rest is zero."""
+    return np.array_equal(g[: r.size], r) and not g[r.size:].any()
+
+
+def _workers_slab(threads, S, frames_per_warp=32):
+    fp = (S + 15) // 16 * 16
+    return 16 + (threads - 32) // 32 * frames_per_warp * fp
+
+
+@pytest.mark.parametrize("teams,threads,S,width", [
+    (3, 64, 64, 0),       # one worker warp
+    (5, 256, 256, 0),     # seven worker warps
+    (4, 160, 100, 45),    # ragged width: warps of 32 and 13 workers, one idle
+    (2, 1024, 36, 0),     # 31 worker warps, frames of 9 words
+    (7, 96, 1028, 33),    # frames of 257 words, a warp with one worker
+    (1, 128, 4, 1),       # one worker, one word
+])
+def test_workers_parity(rt, teams, threads, S, width):
+    work = wl.workers(teams=teams, threads=threads, frame_bytes=S, width=width)
+    g, gs, r, rs = _run_both(rt, work, slab=_workers_slab(threads, S))
+    assert _same_out(g, r)
+    _assert_status_equal(gs, rs)
+    assert (gs["status"] == 0).all() and (gs["depth_final"] == 0).all()
+
+
+def test_workers_spill_to_overflow_shares(rt):
+    S, fp = 200, 208
+    work = wl.workers(teams=6, threads=96, frame_bytes=S, width=40)
+    # slab shares of 10 frames, overflow shares of 22; then all in overflow
+    for slab, ovf in [(16 + 2 * 10 * fp, 2 * 22 * fp), (0, 16 + 2 * 32 * fp)]:
+        g, gs, r, rs = _run_both(rt, work, slab=slab, ovf=ovf, max_teams=6)
+        assert _same_out(g, r)
+        _assert_status_equal(gs, rs)
+        assert (gs["spill_bytes"] > 0).all()
+
+
+def test_workers_overflow_reports_like_the_oracle(rt):
+    S, fp = 200, 208
+    work = wl.workers(teams=3, threads=96, frame_bytes=S, width=40)
+    g, gs, r, rs = _run_both(rt, work, slab=16 + 2 * 10 * fp, ovf=2 * 10 * fp, max_teams=3)
+    assert _same_out(g, r)  # the workers whose frames fitted, and zeros
+    _assert_status_equal(gs, rs)
+    assert (gs["status"] == 2).all()
+
+
+def test_workers_full_size(rt):
+    """The bench's workload: 1024 teams x 256 threads, 256-byte worker frames
+    (224 frames of 256 bytes per team, 56 KiB of warp stacks)."""
+    work = wl.workers(teams=1024, threads=256, frame_bytes=256)
+    g, gs, r, rs = _run_both(rt, work, slab=_workers_slab(256, 256))
+    assert _same_out(g, r)
+    _assert_status_equal(gs, rs)

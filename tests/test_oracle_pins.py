@@ -8,6 +8,9 @@
 * The nested / hetero programs against invariants that any correct
   implementation satisfies (stack depth back to 0, high-water marks, the
   structure that mix32 being a bijection exposes, placement independence).
+* The worker-level program against its structure (s2 XORs every output,
+  the key follows the worker number across warps, a shared base image) and
+  its per-warp stack accounting.
 """
 import math
 import os
@@ -288,6 +291,104 @@ def test_hetero_visibility_chain():
 
 
 # ---------------------------------------------------------------------------
+# Worker-level sharing (the paper's future work, Sec. 7): structure and
+# stack accounting
+# ---------------------------------------------------------------------------
+def _workers_run(work, slab=1 << 20, ovf=0):
+    out, st = oracle.run_workload(work, slab_bytes=slab, overflow_bytes=ovf)
+    r = work.regions[0]
+    return out.view(np.uint32).reshape(r.teams, r.team_width), st
+
+
+def _workers_with_image(work, img_u32):
+    return wl.Workload("t", work.regions, img_u32.view(np.uint8), work.out_bytes, work.n_status)
+
+
+def test_workers_s2_xors_every_output():
+    """out[t] = (sum of worker t's frame) ^ s2: flipping bits of s2 flips
+    the same bits of every output of that team, and nothing else."""
+    w = wl.workers(teams=3, threads=96, frame_bytes=100)
+    ref, _ = _workers_run(w)
+    img = w.images.view(np.uint32).copy()
+    stride = (16 + 112) // 4
+    img[stride * 1 + 2] ^= 0x00F0F001  # team 1's s2
+    got, _ = _workers_run(_workers_with_image(w, img))
+    assert (got[1] ^ ref[1] == 0x00F0F001).all()
+    assert np.array_equal(got[[0, 2]], ref[[0, 2]])
+
+
+def test_workers_key_follows_the_worker_number():
+    """Worker t's frame is keyed by mix32(s0 + t): raising s0 by k gives
+    worker t the frame worker t + k had, so the outputs shift by k, across
+    warp boundaries too."""
+    w = wl.workers(teams=2, threads=128, frame_bytes=136)  # W' = 96: three warps
+    ref, _ = _workers_run(w)
+    img = w.images.view(np.uint32).copy()
+    k = 37
+    stride = (16 + 144) // 4
+    img[0] = (int(img[0]) + k) & M32  # team 0's s0
+    got, _ = _workers_run(_workers_with_image(w, img))
+    assert np.array_equal(got[0][: 96 - k], ref[0][k:])
+    assert np.array_equal(got[1], ref[1])
+    assert not np.array_equal(got[0], ref[0])
+
+
+def test_workers_every_worker_shares_the_base_image():
+    """Every worker's frame starts from the same base words: changing one
+    base word changes every output of that team (a bijective hash of the
+    word is part of every sum), and two teams with the same image agree."""
+    w = wl.workers(teams=2, threads=64, frame_bytes=64)
+    img = w.images.view(np.uint32).copy()
+    stride = (16 + 64) // 4
+    img[stride: 2 * stride] = img[:stride]
+    same, _ = _workers_run(_workers_with_image(w, img))
+    assert np.array_equal(same[0], same[1])
+    assert len(set(same[0].tolist())) == same.shape[1]  # distinct keys per worker
+    img[4 + 9] ^= 1
+    diff, _ = _workers_run(_workers_with_image(w, img))
+    assert (diff[0] != same[0]).all() and np.array_equal(diff[1], same[1])
+
+
+def test_workers_width_keeps_worker_numbers():
+    """A narrower region runs workers 0 .. width-1 with the same frames."""
+    full, _ = _workers_run(wl.workers(teams=2, threads=128, frame_bytes=40))
+    part, _ = _workers_run(wl.workers(teams=2, threads=128, frame_bytes=40, width=45))
+    assert np.array_equal(part, full[:, :45])
+
+
+def test_workers_stack_accounting_and_placement():
+    """hwm = the master's 16-byte frame + every warp's live worker frames;
+    what the slab shares cannot hold goes to the overflow shares; results
+    do not depend on placement."""
+    S, fp = 200, 208
+    w = wl.workers(teams=2, threads=96, frame_bytes=S, width=40)  # warps of 32 and 8 workers
+    ref, st = _workers_run(w, slab=1 << 20)
+    assert (st["status"] == 0).all() and (st["depth_final"] == 0).all()
+    assert (st["hwm_bytes"] == 16 + 40 * fp).all() and (st["spill_bytes"] == 0).all()
+    assert (st["chk"][:, 0] == ref.sum(axis=1, dtype=np.uint32)).all()
+    # slab shares of 10 frames per warp, overflow shares of 22
+    got, st2 = _workers_run(w, slab=16 + 2 * 10 * fp, ovf=2 * 22 * fp)
+    assert np.array_equal(got, ref) and (st2["status"] == 0).all()
+    assert (st2["spill_bytes"] == 22 * fp).all() and (st2["hwm_bytes"] == 16 + 40 * fp).all()
+    # everything in the overflow slab (the master's frame too)
+    got, st3 = _workers_run(w, slab=0, ovf=16 + 2 * 32 * fp)
+    assert np.array_equal(got, ref) and (st3["spill_bytes"] == 16 + 40 * fp).all()
+
+
+def test_workers_overflow_stops_at_the_first_frame_that_fits_nowhere():
+    S, fp = 200, 208
+    w = wl.workers(teams=1, threads=96, frame_bytes=S, width=40)
+    ref, _ = _workers_run(w)
+    got, st = _workers_run(w, slab=16 + 2 * 10 * fp, ovf=2 * 10 * fp)
+    assert st["status"][0] == oracle.ERR_OVERFLOW and st["depth_final"][0] == 0
+    # warp 0 places 20 of its 32 frames; warp 1 all 8 of its frames
+    assert np.array_equal(got[0, :20], ref[0, :20]) and (got[0, 20:32] == 0).all()
+    assert np.array_equal(got[0, 32:], ref[0, 32:])
+    assert st["hwm_bytes"][0] == 16 + 28 * fp and st["spill_bytes"][0] == 10 * fp
+    assert (st["chk"][0] == 0).all()
+
+
+# ---------------------------------------------------------------------------
 # Stack allocator (Sec. 5.3 shared stack + Sec. 5.2 fallback)
 # ---------------------------------------------------------------------------
 def test_stack_lifo_and_placement():
@@ -324,6 +425,9 @@ def test_invalid_descriptors_rejected():
         wl.Region(wl.PROG_SCALARS, 1, 128, 1, [16], width=97, param=1),
         wl.Region(99, 1, 128, 1, [16]),
         wl.Region(wl.PROG_HETERO, 1, 128, 5, [16] * 4),
+        wl.Region(wl.PROG_WORKERS, 1, 32, 2, [16, 64]),   # no worker warp
+        wl.Region(wl.PROG_WORKERS, 1, 128, 2, [32, 64]),  # master frame is s[4]
+        wl.Region(wl.PROG_WORKERS, 1, 128, 1, [16]),
     ]
     for r in bad:
         st = np.zeros(1, dtype=oracle.STATUS_DTYPE)

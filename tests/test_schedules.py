@@ -351,3 +351,80 @@ def test_paper_scalars_every_schedule_matches_oracle():
     ref = tuple(int(v) for v in out.view(np.uint32))
     results = enumerate_schedules(lambda s: paper_scalars_model(r, a0, s))
     assert len(results) == 924 and set(results) == {ref}  # C(12,6)
+
+
+# ---------------------------------------------------------------------------
+# Worker-level sharing (Sec. 7): every worker is the master of a nested
+# region run by 32 inner threads. The model interleaves the workers' steps
+# and, inside each worker's nested region, its inner threads' steps (the
+# scheduler picks the inner thread too), so schedules mix steps of
+# different workers' nested regions; they are sampled at random.
+# ---------------------------------------------------------------------------
+def workers_model(region, images_u32, sched):
+    m = Machine()
+    Wp = region.team_width
+    S = region.frame_bytes[1]
+    L = S // 4
+    stride = (16 + (S + 15) // 16 * 16) // 4
+    outs, chks = {}, {}
+    for team in range(region.teams):
+        src = team * stride
+        F = m.push(4)
+        for i in range(4):
+            m.mem[F + i] = int(images_u32[src + i])
+
+        def inner(j, g, s1):
+            for w in range(j, L, 32):
+                v = yield ("r", g + w)
+                yield ("w", g + w, mix32((v + s1 + w) & M32))
+
+        def worker(t, team=team, src=src):
+            g = m.FRAMES + 4096 + (team * Wp + t) * L  # this worker's frame
+            s0 = yield ("r", F)
+            key = mix32((s0 + t) & M32)
+            for i in range(L):
+                yield ("w", g + i, int(images_u32[src + 4 + i]) ^ key)
+            s1 = yield ("r", F + 1)
+            pending = []
+            for j in range(32):
+                it = inner(j, g, s1)
+                try:
+                    pending.append([it, next(it)])
+                except StopIteration:
+                    pass
+            while pending:
+                i = sched.choose(len(pending))
+                it, op = pending[i]
+                val = yield op
+                try:
+                    pending[i][1] = it.send(val)
+                except StopIteration:
+                    pending.pop(i)
+            total = 0
+            for i in range(L):
+                v = yield ("r", g + i)
+                total = (total + v) & M32
+            s2 = yield ("r", F + 2)
+            yield ("w", m.OUT + team * Wp + t, total ^ s2)
+
+        m.parallel(sched, [worker(t) for t in range(Wp)])
+        chks[team] = sum(m.mem.get(m.OUT + team * Wp + t, 0) for t in range(Wp)) & M32
+        m.pop(F)
+        for t in range(Wp):
+            outs[team * Wp + t] = m.mem.get(m.OUT + team * Wp + t, 0)
+    return tuple(outs[i] for i in sorted(outs)), tuple(chks[t] for t in sorted(chks))
+
+
+def test_workers_sampled_schedules_match_oracle():
+    for teams, threads, width, S in [(2, 64, 3, 140), (1, 96, 34, 12)]:
+        work = wl.workers(teams=teams, threads=threads, frame_bytes=S, width=width, seed=5)
+        r = work.regions[0]
+        out, st = oracle.run_workload(work, slab_bytes=1 << 20)
+        ref = (tuple(int(v) for v in out.view(np.uint32)),
+               tuple(int(st["chk"][t][0]) for t in range(teams)))
+        imgs = work.images.view(np.uint32)
+        rng = random.Random(99)
+        seen = set()
+        for _ in range(25):
+            seen.add(workers_model(r, imgs, Scheduler(rng=rng)))
+        assert seen == {ref}

@@ -25,6 +25,8 @@ Region programs (see the oracle for their semantics):
                          with N(0,1) values.
   P4  "hetero"         - heterogeneous instances (log-uniform teams and
                          frame sizes, uniform threads and depth).
+  P5  "workers"        - worker-level sharing: every worker pushes its own
+                         frame of S bytes for a nested region on its warp.
 """
 from __future__ import annotations
 
@@ -43,6 +45,7 @@ PROG_SCALARS = 3
 PROG_NESTED = 4
 PROG_SWEEP = 5
 PROG_HETERO = 6
+PROG_WORKERS = 7
 
 MAX_DEPTH = 4
 NESTED_FRAME_WORDS = 16 + 256  # int32 s[16]; int32 arr[256]
@@ -304,6 +307,20 @@ def hetero(n_instances: int = 10000, seed: int = DEFAULT_SEED,
     images = np.concatenate(chunks) if chunks else np.zeros(16, np.uint8)
     return Workload("hetero", regions, images, max(out_off, 16), st_idx,
                     meta=dict(n_instances=len(regions)))
+
+
+# ----------------------------------------------------------------------------
+# Worker-level sharing (the paper's future work, Sec. 7)
+# ----------------------------------------------------------------------------
+def workers(teams: int = 1024, threads: int = 256, frame_bytes: int = 256, width: int = 0,
+            seed: int = DEFAULT_SEED) -> Workload:
+    """Per team an image of int32 s[4] then int32 base[S/4], the pair padded
+    to 16 bytes; uniform int32 words."""
+    assert frame_bytes % 4 == 0 and frame_bytes > 0 and threads >= 64
+    stride = 16 + _pad16(frame_bytes)
+    img = uniform_u32(derive(seed, 7, frame_bytes), teams * stride // 4)
+    r = Region(PROG_WORKERS, teams, threads, 2, [16, frame_bytes], width=width)
+    return Workload("workers", [r], _as_bytes(img), 4 * teams * r.team_width, teams)
 
 
 def poisson_arrivals(n: int, rate_per_s: float, seed: int = DEFAULT_SEED) -> np.ndarray:

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 
 #include "dsr.h"
 #include "dsr_check.cuh"
@@ -51,15 +52,22 @@ using KernelFn = void (*)(dsr_region_desc, const uint8_t *, uint8_t *, dsr_team_
                           uint8_t *, uint64_t, uint32_t, uint64_t);
 
 // Programs whose launches fill the GPU with many teams (P::kDense) are
-// held to 32 registers, so 2048 threads per SM can be resident; the others
-// get up to 64.
+// held to 32 registers, so 2048 threads per SM can be resident; those whose
+// teams are few per SM anyway (wide_regs) get up to 85; the others 64.
+template <class P, class = void>
+struct wide_regs : std::false_type {};
+template <class P>
+struct wide_regs<P, std::void_t<decltype(P::kWideRegs)>> : std::bool_constant<P::kWideRegs> {};
+
 template <class P>
 KernelFn pick(uint32_t threads) {
-  constexpr int k = P::kDense ? 2 : 1;
-  if (threads <= 128) return plain_kernel<P, 128, 8 * k>;
-  if (threads <= 256) return plain_kernel<P, 256, 4 * k>;
-  if (threads <= 512) return plain_kernel<P, 512, 2 * k>;
-  return plain_kernel<P, 1024, 1 * k>;
+  // resident CTAs of 256 threads the register budget is sized for
+  constexpr int k = P::kDense ? 8 : wide_regs<P>::value ? 3 : 4;
+  if (threads <= 128) return plain_kernel<P, 128, 2 * k>;
+  if (threads <= 256) return plain_kernel<P, 256, k>;
+  constexpr int k512 = k / 2 > 1 ? k / 2 : 1, k1024 = k / 4 > 1 ? k / 4 : 1;
+  if (threads <= 512) return plain_kernel<P, 512, k512>;
+  return plain_kernel<P, 1024, k1024>;
 }
 
 KernelFn plain_kernel_for(uint32_t program, uint32_t threads) {

@@ -529,6 +529,9 @@ struct ProgHetero {
 struct ProgWorkers {
   static constexpr uint32_t kProgram = DSR_PROG_WORKERS;
   static constexpr bool kDense = false;
+  // Teams hold large warp stacks, so few fit an SM: the plain kernel gets
+  // a register budget for half the usual resident CTAs.
+  static constexpr bool kWideRegs = true;
 
   __device__ static const uint8_t *image(const Env &e) {
     const dsr_region_desc &d = *e.d;
@@ -571,6 +574,49 @@ struct ProgWorkers {
     pop(s, F, 16);
   }
 
+  // One worker's frame at `g` (shared memory when kSmem, else global): its
+  // sequential fill, its nested region on the warp's 32 lanes, and its
+  // sum, which lane `owner` keeps. The fill and the sum move 16-byte
+  // vectors (lane q takes words 4q .. 4q+3 of each 128-word row), the
+  // nested region single words (lane j takes words w = j mod 32), so data
+  // crosses lanes through the frame, between __syncwarp fork and join.
+  // base: this lane's vector of the image (frames of up to 32 vectors keep
+  // it in a register); larger frames read the image again.
+  template <bool kSmem>
+  __device__ static uint32_t frame(uint8_t *gp, uint32_t L, uint32_t key, uint32_t s1,
+                                   const uint4 *img4, uint4 base, uint32_t nv) {
+    const uint32_t lane = lane_id();
+    // a slab frame is addressed from the shared array itself, so its
+    // accesses are shared-memory instructions with 32-bit addresses
+    uint8_t *g = kSmem ? dsr_smem + static_cast<uint32_t>(reinterpret_cast<uintptr_t>(gp) -
+                                                          reinterpret_cast<uintptr_t>(dsr_smem))
+                       : gp;
+    uint4 *g4 = reinterpret_cast<uint4 *>(g);
+    uint32_t *gw = reinterpret_cast<uint32_t *>(g);
+    for (uint32_t q = lane; q < nv; q += 32u) {
+      uint4 x = nv <= 32u ? base : __ldg(img4 + q);
+      x.x ^= key;
+      x.y ^= key;
+      x.z ^= key;
+      x.w ^= key;
+      g4[q] = x;
+    }
+    const uint32_t *imgw = reinterpret_cast<const uint32_t *>(img4);
+    for (uint32_t w = 4u * nv + lane; w < L; w += 32u) gw[w] = __ldg(imgw + w) ^ key;
+    __syncwarp();  // fork: the nested team
+    for (uint32_t w = lane; w < L; w += 32u) gw[w] = mix32(gw[w] + s1 + w);
+    __syncwarp();  // join
+    uint32_t part = 0;
+    for (uint32_t q = lane; q < nv; q += 32u) {
+      const uint4 x = g4[q];
+      part += x.x + x.y + x.z + x.w;
+    }
+    for (uint32_t w = 4u * nv + lane; w < L; w += 32u) part += gw[w];
+    const uint32_t sum = warp_sum(part);
+    __syncwarp();  // the frame may be reused by the next worker's fill
+    return sum;
+  }
+
   // Every worker thread calls run() once (the region is no wider than the
   // workers); the warp is the unit of work.
   __device__ static void run(const Env &e, uint32_t, uint32_t tid, uint32_t, uint32_t n,
@@ -580,7 +626,7 @@ struct ProgWorkers {
     const uint32_t lanes = min(32u, n - t0);  // workers t0 .. t0 + lanes - 1
     Ctrl *c = ctrl();
     const dsr_region_desc &d = *e.d;
-    const uint32_t L = d.frame_bytes[1] / 4u;
+    const uint32_t L = d.frame_bytes[1] / 4u, nv = L / 4u;
     const uint32_t fp = (d.frame_bytes[1] + 15u) & ~15u;
     // this warp's stack: lane order, first fit into the slab share, then
     // the overflow share
@@ -599,26 +645,16 @@ struct ProgWorkers {
     }
     const uint32_t *F = reinterpret_cast<const uint32_t *>(c->frames[0].ptr);
     const uint32_t s0 = F[0], s1 = F[1], s2 = F[2];
-    const uint32_t *base = reinterpret_cast<const uint32_t *>(image(e) + 16);
+    const uint4 *img4 = reinterpret_cast<const uint4 *>(image(e) + 16);
+    const uint4 base = nv <= 32u && lane < nv ? __ldg(img4 + lane) : make_uint4(0, 0, 0, 0);
     const uintptr_t my = reinterpret_cast<uintptr_t>(mine);
-    // each worker's sequential part: fill its frame (order-free word copy,
-    // done by the warp's lanes)
-    for (uint32_t l = 0; l < pushed; ++l) {
-      uint32_t *g = reinterpret_cast<uint32_t *>(__shfl_sync(0xffffffffu, my, l));
-      const uint32_t key = mix32(s0 + t0 + l);
-      for (uint32_t i = lane; i < L; i += 32u) g[i] = __ldg(base + i) ^ key;
-    }
-    __syncwarp();
     uint32_t result = 0;
     for (uint32_t l = 0; l < pushed; ++l) {
-      // fork of worker t0 + l's nested region: its frame address, by shuffle
-      uint32_t *g = reinterpret_cast<uint32_t *>(__shfl_sync(0xffffffffu, my, l));
-      for (uint32_t w = lane; w < L; w += 32u) g[w] = mix32(g[w] + s1 + w);
-      __syncwarp();  // join
-      // the worker's sum of its frame (wrap-around, order-free: the warp's lanes)
-      uint32_t part = 0;
-      for (uint32_t w = lane; w < L; w += 32u) part += g[w];
-      const uint32_t sum = warp_sum(part);
+      // worker t0 + l: its frame's address reaches the nested team by shuffle
+      uint8_t *g = reinterpret_cast<uint8_t *>(__shfl_sync(0xffffffffu, my, l));
+      const uint32_t key = mix32(s0 + t0 + l);
+      const uint32_t sum = l < in_slab ? frame<true>(g, L, key, s1, img4, base, nv)
+                                       : frame<false>(g, L, key, s1, img4, base, nv);
       if (lane == l) result = sum ^ s2;
     }
     if (lane < pushed)

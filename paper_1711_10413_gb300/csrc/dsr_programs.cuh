@@ -523,8 +523,8 @@ struct ProgHetero {
 // nothing. The frames stay live until the warp's last nested region has
 // run, then are popped in reverse order. The stack pointers never leave
 // registers: every frame has the same size, so lane l's slot follows from
-// l. A frame's address reaches the nested team by a warp shuffle (the
-// frame table of the warp is a register per lane).
+// l. A frame's slot reaches the lanes of the nested team by a warp shuffle
+// (the frame table of the warp is a register per lane).
 // ---------------------------------------------------------------------------
 struct ProgWorkers {
   static constexpr uint32_t kProgram = DSR_PROG_WORKERS;
@@ -574,47 +574,114 @@ struct ProgWorkers {
     pop(s, F, 16);
   }
 
-  // One worker's frame at `g` (shared memory when kSmem, else global): its
-  // sequential fill, its nested region on the warp's 32 lanes, and its
-  // sum, which lane `owner` keeps. The fill and the sum move 16-byte
-  // vectors (lane q takes words 4q .. 4q+3 of each 128-word row), the
-  // nested region single words (lane j takes words w = j mod 32), so data
-  // crosses lanes through the frame, between __syncwarp fork and join.
-  // base: this lane's vector of the image (frames of up to 32 vectors keep
-  // it in a register); larger frames read the image again.
-  template <bool kSmem>
-  __device__ static uint32_t frame(uint8_t *gp, uint32_t L, uint32_t key, uint32_t s1,
-                                   const uint4 *img4, uint4 base, uint32_t nv) {
-    const uint32_t lane = lane_id();
-    // a slab frame is addressed from the shared array itself, so its
-    // accesses are shared-memory instructions with 32-bit addresses
-    uint8_t *g = kSmem ? dsr_smem + static_cast<uint32_t>(reinterpret_cast<uintptr_t>(gp) -
-                                                          reinterpret_cast<uintptr_t>(dsr_smem))
-                       : gp;
-    uint4 *g4 = reinterpret_cast<uint4 *>(g);
-    uint32_t *gw = reinterpret_cast<uint32_t *>(g);
-    for (uint32_t q = lane; q < nv; q += 32u) {
-      uint4 x = nv <= 32u ? base : __ldg(img4 + q);
-      x.x ^= key;
-      x.y ^= key;
-      x.z ^= key;
-      x.w ^= key;
-      g4[q] = x;
+  // The warp's work is done in three phases, each over all of its workers'
+  // frames at once and separated by __syncwarp: the workers' fills, then
+  // every worker's nested region, then each worker's sum, by its own lane.
+  // A phase walks the (frame, element) pairs of a run of frames with the
+  // warp's 32 lanes side by side (Walk), so per-frame overhead is paid once
+  // per warp rather than once per frame. In the nested phase the nested
+  // regions of the warp's workers run concurrently, each word once, as any
+  // schedule of their teams may; the fill moves 16-byte vectors and the
+  // nested region single words, so the data crosses lanes through the
+  // frames. The workers publish their keys and their frames' slot offsets
+  // to the lanes that use them by shuffles.
+  struct Walk {  // element idx = lane + 32 i of frames l0, l0 + 1, ... (cnt each)
+    uint32_t l, q, dl, dq, cnt;
+    __device__ Walk(uint32_t l0, uint32_t cnt_) : cnt(cnt_) {
+      const uint32_t lane = lane_id();
+      l = l0 + lane / cnt;
+      q = lane % cnt;
+      dl = 32u / cnt;
+      dq = 32u % cnt;
     }
-    const uint32_t *imgw = reinterpret_cast<const uint32_t *>(img4);
-    for (uint32_t w = 4u * nv + lane; w < L; w += 32u) gw[w] = __ldg(imgw + w) ^ key;
-    __syncwarp();  // fork: the nested team
-    for (uint32_t w = lane; w < L; w += 32u) gw[w] = mix32(gw[w] + s1 + w);
-    __syncwarp();  // join
-    uint32_t part = 0;
-    for (uint32_t q = lane; q < nv; q += 32u) {
+    __device__ void next() {
+      q += dq;
+      l += dl;
+      if (q >= cnt) {
+        q -= cnt;
+        ++l;
+      }
+    }
+  };
+
+  // Fill of frames l0 .. l1-1 stored back to back (stride fp) from `base`:
+  // G_l = image words ^ key of worker l (key_lane: this lane's worker's key).
+  template <bool kSmem>
+  __device__ static void fill_phase(uint8_t *base, uint32_t fp, uint32_t l0, uint32_t l1,
+                                    uint32_t L, const uint4 *img4, uint32_t key_lane) {
+    const uint32_t nv = L / 4u, tw = L - 4u * nv;
+    if (nv) {
+      const uint32_t total = (l1 - l0) * nv;
+      Walk it(l0, nv);
+      for (uint32_t i = lane_id(); i < ((total + 31u) & ~31u); i += 32u, it.next()) {
+        const uint32_t key = __shfl_sync(0xffffffffu, key_lane, it.l & 31u);
+        if (i < total) {
+          uint4 x = __ldg(img4 + it.q);
+          x.x ^= key;
+          x.y ^= key;
+          x.z ^= key;
+          x.w ^= key;
+          reinterpret_cast<uint4 *>(base + (it.l - l0) * fp)[it.q] = x;
+        }
+      }
+    }
+    if (tw) {  // the last L % 4 words of each frame
+      const uint32_t total = (l1 - l0) * tw;
+      const uint32_t *imgw = reinterpret_cast<const uint32_t *>(img4) + 4u * nv;
+      Walk it(l0, tw);
+      for (uint32_t i = lane_id(); i < ((total + 31u) & ~31u); i += 32u, it.next()) {
+        const uint32_t key = __shfl_sync(0xffffffffu, key_lane, it.l & 31u);
+        if (i < total)
+          reinterpret_cast<uint32_t *>(base + (it.l - l0) * fp)[4u * nv + it.q] =
+              __ldg(imgw + it.q) ^ key;
+      }
+    }
+  }
+
+  // Nested regions of frames l0 .. l1-1: G_l[w] = mix32(G_l[w] + s1 + w).
+  // off_lane: this lane's worker's slot offset from `base`.
+  // Four steps of the walk at a time, their loads issued before any of
+  // their stores (the words are distinct), so the latency of a spilled
+  // frame's words is paid once per four.
+  template <bool kSmem>
+  __device__ static void nested_phase(uint8_t *base, uint32_t l0, uint32_t l1, uint32_t L,
+                                      uint32_t s1, uint32_t off_lane) {
+    constexpr uint32_t kB = 4;
+    const uint32_t total = (l1 - l0) * L;
+    Walk it(l0, L);
+    for (uint32_t i = lane_id(); i < ((total + 32u * kB - 1u) & ~(32u * kB - 1u));
+         i += 32u * kB) {
+      uint32_t *g[kB];
+      uint32_t v[kB], w[kB];
+#pragma unroll
+      for (uint32_t u = 0; u < kB; ++u) {
+        const uint32_t off = __shfl_sync(0xffffffffu, off_lane, it.l & 31u);
+        g[u] = i + 32u * u < total ? reinterpret_cast<uint32_t *>(base + off) + it.q : nullptr;
+        w[u] = it.q;
+        v[u] = g[u] ? *g[u] : 0u;
+        it.next();
+      }
+#pragma unroll
+      for (uint32_t u = 0; u < kB; ++u)
+        if (g[u]) *g[u] = mix32(v[u] + s1 + w[u]);
+    }
+  }
+
+  // A worker's sum of its own frame (its lane alone), the vectors read in
+  // an order rotated by the lane so that lanes meet different banks.
+  __device__ static uint32_t frame_sum_own(const uint8_t *g, uint32_t L) {
+    const uint32_t nv = L / 4u;
+    const uint4 *g4 = reinterpret_cast<const uint4 *>(g);
+    uint32_t part = 0, q = nv ? lane_id() % nv : 0u;
+#pragma unroll 4
+    for (uint32_t k = 0; k < nv; ++k) {
       const uint4 x = g4[q];
       part += x.x + x.y + x.z + x.w;
+      q = q + 1u == nv ? 0u : q + 1u;
     }
-    for (uint32_t w = 4u * nv + lane; w < L; w += 32u) part += gw[w];
-    const uint32_t sum = warp_sum(part);
-    __syncwarp();  // the frame may be reused by the next worker's fill
-    return sum;
+    const uint32_t *gw = reinterpret_cast<const uint32_t *>(g);
+    for (uint32_t w = 4u * nv; w < L; ++w) part += gw[w];
+    return part;
   }
 
   // Every worker thread calls run() once (the region is no wider than the
@@ -626,7 +693,7 @@ struct ProgWorkers {
     const uint32_t lanes = min(32u, n - t0);  // workers t0 .. t0 + lanes - 1
     Ctrl *c = ctrl();
     const dsr_region_desc &d = *e.d;
-    const uint32_t L = d.frame_bytes[1] / 4u, nv = L / 4u;
+    const uint32_t L = d.frame_bytes[1] / 4u;
     const uint32_t fp = (d.frame_bytes[1] + 15u) & ~15u;
     // this warp's stack: lane order, first fit into the slab share, then
     // the overflow share
@@ -634,32 +701,32 @@ struct ProgWorkers {
     const uint64_t ovf_fit = c->wovf_bytes / fp;
     const uint32_t pushed =
         static_cast<uint32_t>(min(static_cast<uint64_t>(lanes), in_slab + ovf_fit));
-    uint8_t *mine = nullptr;
-    if (lane < pushed)
-      mine = lane < in_slab ? dsr_smem + c->wstack_off + warp * c->wslab + lane * fp
-                            : c->wovf + warp * c->wovf_bytes + static_cast<uint64_t>(lane - in_slab) * fp;
     if (lane == 0) {
       atomicAdd(&c->whwm, pushed * fp);
       atomicAdd(&c->wspill, (pushed - min(pushed, in_slab)) * fp);
       if (pushed < lanes) atomicOr(&c->wfail, 1u);
     }
+    uint8_t *sbase = dsr_smem + c->wstack_off + warp * c->wslab;  // slab share
+    uint8_t *gbase = c->wovf + warp * c->wovf_bytes;               // overflow share
     const uint32_t *F = reinterpret_cast<const uint32_t *>(c->frames[0].ptr);
     const uint32_t s0 = F[0], s1 = F[1], s2 = F[2];
     const uint4 *img4 = reinterpret_cast<const uint4 *>(image(e) + 16);
-    const uint4 base = nv <= 32u && lane < nv ? __ldg(img4 + lane) : make_uint4(0, 0, 0, 0);
-    const uintptr_t my = reinterpret_cast<uintptr_t>(mine);
-    uint32_t result = 0;
-    for (uint32_t l = 0; l < pushed; ++l) {
-      // worker t0 + l: its frame's address reaches the nested team by shuffle
-      uint8_t *g = reinterpret_cast<uint8_t *>(__shfl_sync(0xffffffffu, my, l));
-      const uint32_t key = mix32(s0 + t0 + l);
-      const uint32_t sum = l < in_slab ? frame<true>(g, L, key, s1, img4, base, nv)
-                                       : frame<false>(g, L, key, s1, img4, base, nv);
-      if (lane == l) result = sum ^ s2;
-    }
-    if (lane < pushed)
+    // each worker's key and its frame's slot offset in its share
+    const uint32_t key = mix32(s0 + t0 + lane);
+    const uint32_t off = lane < in_slab ? lane * fp : (lane - in_slab) * fp;
+    // the workers' sequential parts: their fills (order-free word copies)
+    fill_phase<true>(sbase, fp, 0, in_slab, L, img4, key);
+    if (pushed > in_slab) fill_phase<false>(gbase, fp, in_slab, pushed, L, img4, key);
+    __syncwarp();  // fork of the nested regions
+    nested_phase<true>(sbase, 0, in_slab, L, s1, off);
+    if (pushed > in_slab) nested_phase<false>(gbase, in_slab, pushed, L, s1, off);
+    __syncwarp();  // join
+    if (lane < pushed) {
+      const uint32_t sum = lane < in_slab ? frame_sum_own(sbase + off, L)
+                                          : frame_sum_own(gbase + off, L);
       reinterpret_cast<uint32_t *>(e.out + d.out_offset)[static_cast<uint64_t>(e.team) * n + t0 +
-                                                          lane] = result;
+                                                          lane] = sum ^ s2;
+    }
     // the warp's frames are popped in reverse order: with register stack
     // pointers that is the end of the region
   }

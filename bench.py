@@ -341,12 +341,18 @@ def measure_batched(dsr, torch, rt, flush, sm_count, instances=10000, tuning=Non
     err, counted = rt.batch_errors(b)
     ms_plain = _event_ms(torch, lambda: rt.launch_regions(b), 2, flush)
     st = b["status"].cpu().numpy().view(dsr.TEAM_STATUS_DTYPE)
+    # the same per-instance launches with each launch's slab sized from its
+    # region's footprint instead of one 16 KiB slab for all
+    rt.configure(dsr.DSR_SLAB_AUTO, 3 * 32768, 4096)
+    ms_auto = _event_ms(torch, lambda: rt.launch_regions(b), 2, flush)
+    rt.configure(16384, 3 * 32768, 4096)
     stack = hetero_stack_bytes(work.regions)
     smem_gbs = stack / (ms_batch * 1e-3) / 1e9
     forms["batched"] = dict(workload="hetero_%d_instances" % instances, instances=instances,
                             teams=counted, tuning=tuning,
                             batched_regions_per_s=instances / (ms_batch * 1e-3),
                             per_launch_regions_per_s=instances / (ms_plain * 1e-3),
+                            per_launch_auto_slab_regions_per_s=instances / (ms_auto * 1e-3),
                             batched_push_pop_per_s=sum(r.teams * r.depth for r in work.regions)
                             / (ms_batch * 1e-3),
                             speedup=ms_plain / ms_batch,

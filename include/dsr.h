@@ -44,6 +44,7 @@ extern "C" {
 #define DSR_MAX_FRAMES 8     /* frame-table entries per team stack */
 #define DSR_MAX_THREADS 1024 /* threads per team, master warp included */
 #define DSR_PENDING (-1)     /* dsr_serve_poll: the request has not completed */
+#define DSR_SLAB_AUTO 0xFFFFFFFFu /* dsr_stack_init: size each plain launch's slab */
 
 typedef enum dsr_status {
   DSR_OK = 0,
@@ -162,7 +163,11 @@ const char *dsr_last_error_string(const dsr_ctx *ctx);
 
 /* Configure every team's stack: a shared-memory slab of smem_slab_bytes
  * (multiple of 16, at most what one CTA can hold next to the control
- * block) and a global overflow slab of overflow_bytes_per_team, carved for
+ * block; or DSR_SLAB_AUTO: every plain launch sizes its slab to the
+ * region's dsr_region_footprint, capped at what a CTA can hold -- the
+ * shared memory is then allocated per region from an estimate of its need
+ * rather than preallocated, the paper's proposal of Sec. 7) and a global
+ * overflow slab of overflow_bytes_per_team, carved for
  * team t at overflow_pool_dev + t * overflow_bytes_per_team. The pool is a
  * caller-owned device buffer of pool_bytes (16-byte aligned) that the ctx
  * borrows; max_teams * overflow_bytes_per_team must fit in it. A push that
@@ -184,6 +189,17 @@ int32_t dsr_validate_region(const dsr_region_desc *d, uint64_t image_bytes, uint
  * (any pointer may be NULL). DSR_ERR_INVALID for a malformed descriptor. */
 int32_t dsr_region_extent(const dsr_region_desc *d, uint64_t *image_bytes, uint64_t *out_bytes,
                           uint64_t *n_status);
+
+/* Stack footprint of a region's teams, from its descriptor alone: the
+ * bytes its stack holds at its deepest point (*stack_bytes, the hwm_bytes a
+ * team reports when nothing spills) and the shared-memory slab that keeps
+ * every frame out of the overflow slab under the runtime's placement
+ * (*slab_bytes; for DSR_PROG_WORKERS the warp stacks' even shares make it
+ * larger than the stack bytes when the region width is not a multiple of
+ * 32). The estimate the paper proposes for sizing shared memory (Sec. 7).
+ * Either pointer may be NULL. DSR_ERR_INVALID for a malformed descriptor. */
+int32_t dsr_region_footprint(const dsr_region_desc *d, uint64_t *stack_bytes,
+                             uint64_t *slab_bytes);
 
 /* Footprint and occupancy model of a team shape (threads, frame sizes of
  * one descriptor, slab size) on a GB300-class SM: 228 KB shared memory per

@@ -22,6 +22,7 @@ DSR_ERR_BUDGET, DSR_ERR_TIMEOUT, DSR_ERR_CUDA = 4, 5, 6
 DSR_MAX_DEPTH = 4
 DSR_MAX_FRAMES = 8
 DSR_PENDING = -1
+DSR_SLAB_AUTO = 0xFFFFFFFF
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OVERFLOW", 3: "LIFO", 4: "BUDGET", 5: "TIMEOUT",
                 6: "CUDA"}
 
@@ -108,6 +109,7 @@ def _declare(L):
         "dsr_region_extent": (_i32, [P(dsr_region_desc), P(_u64), P(_u64), P(_u64)]),
         "dsr_footprint_model": (_i32, [P(dsr_region_desc), _u32, _u32, P(dsr_footprint)]),
         "dsr_region_occupancy": (_i32, [_vp, P(dsr_region_desc), P(dsr_occupancy)]),
+        "dsr_region_footprint": (_i32, [P(dsr_region_desc), P(_u64), P(_u64)]),
         "dsr_launch_region": (_i32, [_vp, P(dsr_region_desc), _vp, _u64, _vp, _u64, _vp, _u64,
                                      _vp]),
         "dsr_run_region_host": (_i32, [_vp, P(dsr_region_desc), _vp, _u64, _vp, _u64, _vp,
@@ -158,7 +160,7 @@ def build(force: bool = False) -> str:
 def exported_symbols():
     return ["dsr_create", "dsr_destroy", "dsr_last_error_string", "dsr_stack_init",
             "dsr_validate_region", "dsr_region_extent", "dsr_footprint_model",
-            "dsr_region_occupancy",
+            "dsr_region_occupancy", "dsr_region_footprint",
             "dsr_launch_region", "dsr_run_region_host", "dsr_batch_workspace_bytes",
             "dsr_batch_count", "dsr_launch_batch", "dsr_batch_errors", "dsr_autotune",
             "dsr_launch_regions", "dsr_launch_batch_static", "dsr_batch_static_capacity",
@@ -265,6 +267,14 @@ def dsr_footprint_model(region, slab_bytes: int, regs: int = 0) -> dict:
     f = dsr_footprint()
     _check(lib().dsr_footprint_model(ctypes.byref(d), slab_bytes, regs, ctypes.byref(f)))
     return {k: getattr(f, k) for k, _ in dsr_footprint._fields_}
+
+
+def dsr_region_footprint(region):
+    """(peak stack bytes, slab bytes that hold every frame) of a region."""
+    d = pack_desc(region)
+    a, b = _u64(), _u64()
+    _check(lib().dsr_region_footprint(ctypes.byref(d), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def dsr_region_occupancy(ctx: int, region) -> dict:

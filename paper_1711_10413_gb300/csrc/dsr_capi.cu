@@ -186,14 +186,7 @@ extern "C" int32_t dsr_footprint_model(const dsr_region_desc *d, uint32_t slab_b
   if (regs > 255) return dsr_fail(nullptr, DSR_ERR_INVALID, "regs > 255");
   // frames of one team are all live at the deepest point: place them in
   // push order, first fit into the slab, else the overflow slab
-  uint64_t sp = 0, spill = 0;
-  for (uint32_t k = 0; k < d->depth; ++k) {
-    const uint64_t fp = dsr::pad16(d->frame_bytes[k]);
-    if (sp + fp <= slab_bytes)
-      sp += fp;
-    else
-      spill += fp;
-  }
+  const uint64_t spill = dsr::spill_bytes(*d, slab_bytes);
   const uint32_t warps = d->threads / 32;
   const uint32_t smem = kCtrlBytes + slab_bytes;
   const uint32_t by_threads = kWarpsPerSm / warps;
@@ -267,10 +260,31 @@ static int32_t set_smem_attr(dsr_ctx *ctx, uint32_t smem) {
   return DSR_OK;
 }
 
+extern "C" int32_t dsr_region_footprint(const dsr_region_desc *d, uint64_t *stack_bytes,
+                                        uint64_t *slab_bytes) {
+  const char *why;
+  if (dsr_check_shape(d, &why) != DSR_OK) return dsr_fail(nullptr, DSR_ERR_INVALID, "%s", why);
+  uint64_t st, sl;
+  dsr::footprint(*d, &st, &sl);
+  if (stack_bytes) *stack_bytes = st;
+  if (slab_bytes) *slab_bytes = sl;
+  return DSR_OK;
+}
+
+uint32_t dsr_plain_slab(const dsr_ctx *ctx, const dsr_region_desc *d) {
+  if (!ctx->slab_auto) return ctx->slab_bytes;
+  uint64_t st, sl;
+  dsr::footprint(*d, &st, &sl);
+  return static_cast<uint32_t>(sl < ctx->slab_bytes ? dsr::pad16(sl) : ctx->slab_bytes);
+}
+
 extern "C" int32_t dsr_stack_init(dsr_ctx *ctx, uint32_t smem_slab_bytes,
                                   uint64_t overflow_bytes_per_team, uint32_t max_teams,
                                   void *overflow_pool_dev, uint64_t pool_bytes) {
   if (!ctx) return dsr_fail(nullptr, DSR_ERR_INVALID, "null ctx");
+  const bool slab_auto = smem_slab_bytes == DSR_SLAB_AUTO;
+  if (slab_auto)  // the cap: what one CTA can hold next to the control block
+    smem_slab_bytes = (static_cast<uint32_t>(ctx->max_smem_optin) - kCtrlBytes) & ~15u;
   if (smem_slab_bytes % 16 || overflow_bytes_per_team % 16)
     return dsr_fail(ctx, DSR_ERR_INVALID, "slab sizes must be multiples of 16");
   if (kCtrlBytes + smem_slab_bytes > static_cast<uint32_t>(ctx->max_smem_optin))
@@ -290,6 +304,7 @@ extern "C" int32_t dsr_stack_init(dsr_ctx *ctx, uint32_t smem_slab_bytes,
   rc = dsr_ctx_stack_changed(ctx, kCtrlBytes + smem_slab_bytes);
   if (rc != DSR_OK) return rc;
   ctx->slab_bytes = smem_slab_bytes;
+  ctx->slab_auto = slab_auto;
   ctx->ovf_per_team = overflow_bytes_per_team;
   ctx->max_teams = overflow_bytes_per_team ? max_teams : 0xffffffffu;
   ctx->pool = static_cast<uint8_t *>(overflow_pool_dev);
@@ -306,9 +321,10 @@ int32_t dsr_launch_plain(dsr_ctx *ctx, const dsr_region_desc *d, const void *ima
   // a team without workers gets one worker warp (its region width is 1)
   const uint32_t block = d->threads > 32u ? d->threads : 64u;
   KernelFn k = plain_kernel_for(d->program, block);
-  k<<<d->teams, block, kCtrlBytes + ctx->slab_bytes, s>>>(
+  const uint32_t slab = dsr_plain_slab(ctx, d);
+  k<<<d->teams, block, kCtrlBytes + slab, s>>>(
       *d, static_cast<const uint8_t *>(images_dev), static_cast<uint8_t *>(out_dev), status_dev,
-      ctx->pool, ctx->ovf_per_team, ctx->slab_bytes, ctx->timeout_ns);
+      ctx->pool, ctx->ovf_per_team, slab, ctx->timeout_ns);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "plain launch");
   return DSR_OK;
@@ -352,7 +368,8 @@ extern "C" int32_t dsr_region_occupancy(dsr_ctx *ctx, const dsr_region_desc *d,
   if (dsr_check_shape(d, &why) != DSR_OK) return dsr_fail(ctx, DSR_ERR_INVALID, "%s", why);
   const uint32_t block = d->threads > 32u ? d->threads : 64u;
   const void *k = reinterpret_cast<const void *>(plain_kernel_for(d->program, block));
-  const uint32_t smem = kCtrlBytes + ctx->slab_bytes;
+  const uint32_t slab = dsr_plain_slab(ctx, d);
+  const uint32_t smem = kCtrlBytes + slab;
   cudaFuncAttributes a{};
   int per_sm = 0;
   cudaError_t e = cudaSetDevice(ctx->device);
@@ -361,15 +378,7 @@ extern "C" int32_t dsr_region_occupancy(dsr_ctx *ctx, const dsr_region_desc *d,
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, static_cast<int>(block),
                                                       static_cast<size_t>(smem));
   if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "occupancy query");
-  // frames in push order, first fit into the slab, else the overflow slab
-  uint64_t sp = 0, spill = 0;
-  for (uint32_t i = 0; i < d->depth; ++i) {
-    const uint64_t fp = dsr::pad16(d->frame_bytes[i]);
-    if (sp + fp <= ctx->slab_bytes)
-      sp += fp;
-    else
-      spill += fp;
-  }
+  const uint64_t spill = dsr::spill_bytes(*d, slab);
   out->threads = block;
   out->regs_per_thread = static_cast<uint32_t>(a.numRegs);
   out->smem_per_team = smem;

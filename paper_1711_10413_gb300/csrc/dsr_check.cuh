@@ -84,6 +84,51 @@ DSR_HD void extent(const dsr_region_desc &d, uint64_t *ib, uint64_t *ob, uint64_
   *ns = T;
 }
 
+// Peak stack bytes of a well-formed descriptor's teams, and the slab that
+// holds all of them under the placement rules (first fit; the worker
+// program's warp stacks get even shares of the slab left after the master's
+// 16-byte frame).
+DSR_HD void footprint(const dsr_region_desc &d, uint64_t *stack, uint64_t *slab) {
+  uint64_t st = 0, sl = 0;
+  switch (d.program) {
+    case DSR_PROG_WORKERS: {
+      const uint64_t W = d.threads - 32u, w = desc_width(d), fp = pad16(d.frame_bytes[1]);
+      const uint64_t per_warp = w < 32u ? w : 32u;
+      st = 16u + w * fp;
+      sl = 16u + (W / 32u) * per_warp * fp;
+      break;
+    }
+    default:  // every frame live at the deepest point
+      for (uint32_t k = 0; k < d.depth; ++k) st += pad16(d.frame_bytes[k]);
+      sl = st;
+  }
+  *stack = st;
+  *slab = sl;
+}
+
+// Bytes per team that a slab of `slab` bytes leaves to the overflow slab
+// (which is assumed large enough): first fit in push order; for the worker
+// program, the master's frame first and then each warp's frames in its
+// even share of what is left.
+DSR_HD uint64_t spill_bytes(const dsr_region_desc &d, uint64_t slab) {
+  uint64_t sp = 0, spill = 0;
+  if (d.program == DSR_PROG_WORKERS) {
+    if (slab >= 16u) sp = 16u; else spill = 16u;
+    const uint64_t W = d.threads - 32u, w = desc_width(d), fp = pad16(d.frame_bytes[1]);
+    const uint64_t nwarps = W / 32u, share = ((slab - sp) / nwarps) & ~static_cast<uint64_t>(15u);
+    for (uint64_t t0 = 0; t0 < w; t0 += 32u) {
+      const uint64_t lanes = w - t0 < 32u ? w - t0 : 32u, fit = share / fp;
+      spill += (lanes > fit ? lanes - fit : 0u) * fp;
+    }
+    return spill;
+  }
+  for (uint32_t k = 0; k < d.depth; ++k) {
+    const uint64_t fp = pad16(d.frame_bytes[k]);
+    if (sp + fp <= slab) sp += fp; else spill += fp;
+  }
+  return spill;
+}
+
 // The descriptor fits the buffers it indexes.
 DSR_HD bool fits(const dsr_region_desc &d, uint64_t image_bytes, uint64_t out_bytes,
                  uint64_t n_status) {

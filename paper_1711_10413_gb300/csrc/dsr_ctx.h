@@ -19,7 +19,8 @@ struct dsr_ctx {
   uint64_t timeout_ns = 1000000000ull;
   // stacks (dsr_stack_init)
   bool stack_ready = false;
-  uint32_t slab_bytes = 0;
+  uint32_t slab_bytes = 0;  // with slab_auto: the cap (what a CTA can hold)
+  bool slab_auto = false;   // each plain launch sizes its slab to its region
   uint64_t ovf_per_team = 0;
   uint32_t max_teams = 0;
   uint8_t *pool = nullptr;
@@ -35,6 +36,9 @@ int32_t dsr_fail(dsr_ctx *ctx, int32_t code, const char *fmt, ...);
 int32_t dsr_cuda_fail(dsr_ctx *ctx, cudaError_t e, const char *what);
 // Descriptor shape checks shared by every launch form.
 int32_t dsr_check_shape(const dsr_region_desc *d, const char **why);
+// Slab of a plain launch of *d: the configured slab, or with DSR_SLAB_AUTO
+// the region's footprint slab capped at what a CTA can hold.
+uint32_t dsr_plain_slab(const dsr_ctx *ctx, const dsr_region_desc *d);
 // The plain launch itself (arguments already checked).
 int32_t dsr_launch_plain(dsr_ctx *ctx, const dsr_region_desc *d, const void *images_dev,
                          void *out_dev, dsr_team_status *status_dev, cudaStream_t s);

@@ -106,3 +106,53 @@ def test_occupancy_rejects_missing_context(L):
     with pytest.raises(dsr.DsrError) as ei:
         dsr.dsr_region_occupancy(None, r)
     assert ei.value.code == dsr.DSR_ERR_INVALID
+
+
+def _oracle_rows(work, i, slab, ovf):
+    import oracle
+    _, st = oracle.run_workload(work, slab_bytes=slab, overflow_bytes=ovf, regions=[i])
+    r = work.regions[i]
+    return st[r.status_index: r.status_index + r.teams]
+
+
+def _footprint_cases():
+    cases = [wl.paper_scalars(7, teams=2), wl.paper_scalars(40, teams=2, threads=64),
+             wl.paper_arrays(3, teams=2), wl.scalars(5, teams=2),
+             wl.hetero(25, max_teams=3, max_frame=4096)]
+    cases += [wl.nested(teams=2, threads=128, depth=d, elems_per_team=8) for d in (1, 2, 3, 4)]
+    cases += [wl.sweep(S, teams=2) for S in (4, 20, 1092, 8192)]
+    cases += [wl.workers(teams=2, threads=t, frame_bytes=S, width=w)
+              for t, S, w in [(64, 64, 0), (256, 100, 0), (160, 36, 45), (96, 4, 1), (1024, 20, 0)]]
+    return cases
+
+
+def test_region_footprint_matches_the_oracles_stack(L):
+    """The library's footprint estimate (host code, from the descriptor
+    alone) against the oracle's stack accounting: the peak stack bytes equal
+    the hwm a team reports, and the slab estimate is tight -- with it
+    nothing spills, with 16 bytes less something does."""
+    for work in _footprint_cases():
+        for i, r in enumerate(work.regions):
+            stack, slab = dsr.dsr_region_footprint(r)
+            assert slab % 16 == 0 and slab >= stack
+            rows = _oracle_rows(work, i, 1 << 40, 0)
+            assert (rows["status"] == 0).all()
+            assert (rows["hwm_bytes"] == stack).all(), (work.name, r)
+            rows = _oracle_rows(work, i, slab, 1 << 30)
+            assert (rows["status"] == 0).all() and (rows["spill_bytes"] == 0).all()
+            rows = _oracle_rows(work, i, slab - 16, 1 << 30)
+            assert (rows["status"] == 0).all() and (rows["spill_bytes"] > 0).all(), (work.name, r)
+
+
+def test_footprint_model_spill_matches_the_oracle(L):
+    """dsr_footprint_model's bytes per team left to the overflow slab, for a
+    slab between nothing and everything, against the oracle's spill."""
+    for work in _footprint_cases():
+        for i, r in enumerate(work.regions):
+            _, slab = dsr.dsr_region_footprint(r)
+            for sl in {0, 16, slab // 2 // 16 * 16, slab - 16, slab}:
+                if sl + 384 > 232448:
+                    continue
+                model = dsr.dsr_footprint_model(r, sl, 32)["spill_bytes"]
+                rows = _oracle_rows(work, i, sl, 1 << 30)
+                assert (rows["spill_bytes"] == model).all(), (work.name, r, sl)

@@ -272,3 +272,27 @@ def test_workers_full_size(rt):
     g, gs, r, rs = _run_both(rt, work, slab=_workers_slab(256, 256))
     assert _same_out(g, r)
     _assert_status_equal(gs, rs)
+
+
+# ---------------------------------------------------------------------------
+# Shared memory sized per launch from the footprint estimate (DSR_SLAB_AUTO)
+# ---------------------------------------------------------------------------
+def test_auto_slab_holds_every_frame(rt):
+    import paper_1711_10413_gb300 as dsr
+    works = [wl.nested(teams=16, threads=256, depth=3), wl.sweep(98304, teams=8),
+             wl.workers(teams=6, threads=160, frame_bytes=100, width=45),
+             wl.hetero(30, max_teams=8, max_frame=8192), wl.paper_arrays(2, teams=3)]
+    for work in works:
+        rt.configure(dsr.DSR_SLAB_AUTO, 0, 0)
+        for region in work.regions:
+            occ = rt.occupancy(region)
+            assert occ["smem_per_team"] == 384 + dsr.dsr_region_footprint(region)[1]
+            assert occ["spill_bytes"] == 0
+        g, gs = rt.run_workload(work)
+        r, rs = oracle.run_workload(work, slab_bytes=1 << 40, overflow_bytes=0)
+        if work.out_dtype == "float32":
+            _check_sweep(work, g, r)
+        else:
+            assert _same_out(g, r)
+        _assert_status_equal(gs, rs)
+        assert (gs["spill_bytes"] == 0).all() and (gs["status"] == 0).all()

@@ -215,7 +215,7 @@ def hetero_stack_bytes(regions) -> int:
 
 
 def measure_sweep(dsr, torch, device, flush, hbm_gbs, sizes=None):
-    """Config 3: one fp32 frame per team, 512 teams x 128 threads, for each
+    """The sweep: one fp32 frame per team, 512 teams x 128 threads, for each
     frame size placed in the shared-memory slab (when one CTA can hold it)
     and in the global overflow slab; HBM bytes per launch = images read +
     outputs + statuses."""
@@ -310,7 +310,7 @@ def measure_forms(dsr, torch, device, flush, hbm_gbs, which=FORMS, instances=100
 
 def measure_scalars(dsr, torch, rt, flush):
     forms = {}
-    # config 1: 1000 sequential regions of one team
+    # scalars: 1000 sequential regions of one team
     sc = wl.scalars(n_regions=1000, teams=1, threads=128)
     one = wl.scalars(n_regions=1, teams=1, threads=128)
     rt.configure(1024, 3 * 32768, 4096)
@@ -331,7 +331,7 @@ def measure_scalars(dsr, torch, rt, flush):
 
 def measure_batched(dsr, torch, rt, flush, sm_count, instances=10000, tuning=None):
     forms = {}
-    # config 4: batched vs per-launch
+    # hetero instances: batched vs per-launch
     rt.configure(16384, 3 * 32768, 4096)
     work = wl.hetero(n_instances=instances)
     b = rt.batch_buffers(work)
@@ -370,7 +370,7 @@ def measure_batched(dsr, torch, rt, flush, sm_count, instances=10000, tuning=Non
 
 def measure_served(dsr, rt):
     forms = {}
-    # config 5: served at several rates vs per-request launches. 100,000
+    # hetero requests: served at several rates vs per-request launches. 100,000
     # requests per rate cycle over 20,000 distinct instances (a request's
     # twins rewrite the same output rows with the same values); the first
     # 10 % of each run are warm-up and not counted in the percentiles.

@@ -90,7 +90,7 @@ struct ProgPaperArrays {
 };
 
 // ---------------------------------------------------------------------------
-// Config 1: R = param sequential regions per team, each pushing int32 s[4]
+// Scalars program: R = param sequential regions per team, each pushing int32 s[4]
 // from image[r]; out[(r*T + team)*W' + tid] = (s0*tid + s1) ^
 // ((s2 >> (tid & 7)) + s3). The master warp loads the frames of the next
 // 32 regions while the current ones run (one region per lane).
@@ -141,7 +141,7 @@ struct ProgScalars {
 };
 
 // ---------------------------------------------------------------------------
-// Config 2: D nested master-side calls. Level k pushes F_k = {int32 s[16];
+// Nested program: D nested master-side calls. Level k pushes F_k = {int32 s[16];
 // int32 arr[256]} filled from image[team][k-1] XOR mix32(team*8 + k), with
 // F_k.s[0] ^= F_{k-1}.s[15] for k > 1, then forks:
 //   k < D: F_k.arr[i] = mix32(F_k.arr[i] + i) for the worker's strided i;
@@ -330,7 +330,7 @@ struct ProgNested {
 };
 
 // ---------------------------------------------------------------------------
-// Config 3: one frame float arr[L] (L = frame_bytes/4) copied from
+// Sweep program: one frame float arr[L] (L = frame_bytes/4) copied from
 // image[team]; out[team*W' + tid] = arr[tid] + arr[tid + W'] + ... in index
 // order, each addition rounded to fp32 (no contraction). A large frame in
 // the slab is filled by a streamed fill (the region's argument is then 1):
@@ -395,7 +395,7 @@ struct ProgSweep {
 };
 
 // ---------------------------------------------------------------------------
-// Config 4/5: D levels of F_k = int32[L_k] filled from the instance's level
+// Hetero program (heterogeneous instances): D levels of F_k = int32[L_k] filled from the instance's level
 // images XOR mix32(salt + team*8 + k), F_k[0] ^= c_{k-1} for k > 1, then:
 //   k < D: F_k[w] = mix32(F_k[w] + w) for the worker's strided w; after the
 //          join the master sums F_k into c_k (= chk[k-1]);

@@ -44,7 +44,7 @@ def test_batch_small_full_parity(rt):
         assert (gs["status"] == 0).all() and (gs["depth_final"] == 0).all()
 
 
-def test_batch_config4_full_sampled(rt):
+def test_batch_10000_instances_sampled(rt):
     """10,000 instances in one persistent launch; the oracle checks a seeded
     sample of instances plus the largest and the widest ones."""
     work = wl.hetero(n_instances=10000)

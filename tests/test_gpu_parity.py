@@ -65,9 +65,9 @@ def test_paper_arrays(rt, n_arrays):
 
 
 # ---------------------------------------------------------------------------
-# Config 1: 1 team x 128 threads, 1000 sequential regions
+# Scalars: 1 team x 128 threads, 1000 sequential regions
 # ---------------------------------------------------------------------------
-def test_scalars_config1_full(rt):
+def test_scalars_1000_regions_full(rt):
     work = wl.scalars(n_regions=1000, teams=1, threads=128)
     g, gs, r, rs = _run_both(rt, work, slab=1024)
     assert np.array_equal(g, r)
@@ -87,9 +87,9 @@ def test_scalars_shapes(rt, teams, threads, width):
 
 
 # ---------------------------------------------------------------------------
-# Config 2: 1024 teams x 256 threads, 3 nested levels, 4M int32 output
+# Nested: 1024 teams x 256 threads, 3 nested levels, 4M int32 output
 # ---------------------------------------------------------------------------
-def test_nested_config2_full(rt):
+def test_nested_1024x256_full(rt):
     work = wl.nested(teams=1024, threads=256, depth=3, elems_per_team=4096)
     g, gs, r, rs = _run_both(rt, work, slab=3264)
     assert g.size == 4 * 1024 * 1024
@@ -127,7 +127,7 @@ def test_nested_overflow_failure_reports(rt):
 
 
 # ---------------------------------------------------------------------------
-# Config 3: FP32 sweep, 512 teams x 128 threads, frames 64 B .. 192 KiB
+# Sweep: FP32, 512 teams x 128 threads, frames 64 B .. 192 KiB
 # ---------------------------------------------------------------------------
 def _check_sweep(work, g, ref):
     r = work.regions[0]
@@ -150,7 +150,7 @@ def _check_sweep(work, g, ref):
 
 @pytest.mark.parametrize("S", list(wl.SWEEP_SIZES))
 @pytest.mark.parametrize("where", ["smem", "overflow"])
-def test_sweep_config3(rt, S, where):
+def test_sweep_512x128(rt, S, where):
     work = wl.sweep(S, teams=512, threads=128)
     if where == "smem":
         if S + 384 > 232448:
@@ -174,7 +174,7 @@ def test_sweep_ragged(rt, S):
 
 
 # ---------------------------------------------------------------------------
-# Config 4 program, one instance per plain launch
+# Hetero program, one instance per plain launch
 # ---------------------------------------------------------------------------
 def test_hetero_plain_instances(rt):
     work = wl.hetero(n_instances=60, max_teams=40)

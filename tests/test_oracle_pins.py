@@ -3,7 +3,7 @@
 * mix32 against MurmurHash3_x86_32's published test vectors and SMHasher's
   verification value (tests/golden/murmur3_x86_32.txt).
 * The paper's two evaluation programs (Sec. 6.1) against their closed forms.
-* The config-1 body against hand-evaluated values (tests/golden).
+* The scalars body against hand-evaluated values (tests/golden).
 * The FP32 sweep against exactly rounded sums and closed-form counts.
 * The nested / hetero programs against invariants that any correct
   implementation satisfies (stack depth back to 0, high-water marks, the
@@ -123,7 +123,7 @@ def test_paper_arrays_closed_form(n_arrays):
 
 
 # ---------------------------------------------------------------------------
-# Config-1 body: hand-evaluated values
+# Scalars body: hand-evaluated values
 # ---------------------------------------------------------------------------
 def test_scalars_worked_values(golden_dir):
     rows = [list(map(int, p)) for p in _golden_lines(golden_dir, "scalars_worked.txt")]
@@ -151,7 +151,7 @@ def test_scalars_regions_are_sequential_and_independent():
 
 
 # ---------------------------------------------------------------------------
-# Config-3 FP32 sweep: exact sums and closed-form counts
+# FP32 sweep: exact sums and closed-form counts
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("frame_bytes", [64, 1024, 8192, 4 * 1000])
 def test_sweep_all_ones_counts(frame_bytes):
@@ -187,7 +187,7 @@ def test_sweep_matches_exact_sum(frame_bytes):
 
 
 # ---------------------------------------------------------------------------
-# Config-2 nested program: invariants
+# Nested program: invariants
 # ---------------------------------------------------------------------------
 def test_nested_invariants():
     w = wl.nested(teams=6, threads=256, depth=3, elems_per_team=4096)
@@ -240,7 +240,7 @@ def test_nested_push_failure_unwinds():
 
 
 # ---------------------------------------------------------------------------
-# Config-4 hetero program: invariants
+# Hetero program: invariants
 # ---------------------------------------------------------------------------
 def test_hetero_invariants_and_placement():
     w = wl.hetero(n_instances=40, max_teams=6)

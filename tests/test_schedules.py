@@ -115,7 +115,7 @@ class Machine:
 
 
 # ---------------------------------------------------------------------------
-# The hetero program (config 4), modelled
+# The hetero program (heterogeneous instances), modelled
 # ---------------------------------------------------------------------------
 def hetero_model(region, images_u32, sched):
     m = Machine()
@@ -214,7 +214,7 @@ def test_racy_control_shows_several_outcomes():
 
 
 # ---------------------------------------------------------------------------
-# The nested program (config 2), modelled; 1088-byte frames are too big for
+# The nested program, modelled; 1088-byte frames are too big for
 # exhaustive enumeration, so schedules are sampled at random
 # ---------------------------------------------------------------------------
 def nested_model(region, images_u32, sched):
@@ -276,7 +276,7 @@ def test_nested_sampled_schedules_match_oracle():
 
 
 # ---------------------------------------------------------------------------
-# Config-1 program and the paper's programs: exhaustive on tiny instances
+# The scalars program and the paper's programs: exhaustive on tiny instances
 # ---------------------------------------------------------------------------
 def scalars_model(region, images_u32, sched):
     m = Machine()

@@ -208,7 +208,7 @@ def paper_arrays(n_arrays: int = 1, teams: int = 4, threads: int = 128,
 
 
 # ----------------------------------------------------------------------------
-# Config 1: tiny plain regions
+# Scalars: many tiny sequential regions
 # ----------------------------------------------------------------------------
 def scalars(n_regions: int = 1000, teams: int = 1, threads: int = 128,
             seed: int = DEFAULT_SEED) -> Workload:
@@ -221,7 +221,7 @@ def scalars(n_regions: int = 1000, teams: int = 1, threads: int = 128,
 
 
 # ----------------------------------------------------------------------------
-# Config 2: wide nested regions
+# Nested: wide regions with nested levels
 # ----------------------------------------------------------------------------
 def nested(teams: int = 1024, threads: int = 256, depth: int = 3,
            elems_per_team: int = 4096, seed: int = DEFAULT_SEED) -> Workload:
@@ -233,7 +233,7 @@ def nested(teams: int = 1024, threads: int = 256, depth: int = 3,
 
 
 # ----------------------------------------------------------------------------
-# Config 3: overflow sweep
+# Sweep: one fp32 frame per team, in the slab or spilled
 # ----------------------------------------------------------------------------
 SWEEP_SIZES = (64, 1024, 8192, 32768, 98304, 196608)
 
@@ -249,7 +249,7 @@ def sweep(frame_bytes: int, teams: int = 512, threads: int = 128,
 
 
 # ----------------------------------------------------------------------------
-# Config 4: heterogeneous instances (batched / served)
+# Hetero: heterogeneous instances (batched / served)
 # ----------------------------------------------------------------------------
 def hetero_shapes(n_instances: int, seed: int = DEFAULT_SEED,
                   max_teams: int = 512, max_frame: int = 32768):

@@ -29,6 +29,11 @@
  *  - Device-side errors (stack overflow, LIFO misuse) are written to the
  *    per-team dsr_team_status records; the host reads them after a sync.
  *    No kernel traps.
+ *  - A dsr_ctx is not thread-safe: calls on one ctx must not overlap (use
+ *    one ctx per host thread). The host-side checks that take no ctx
+ *    (dsr_validate_region, dsr_region_extent, dsr_region_footprint,
+ *    dsr_footprint_model, dsr_batch_workspace_bytes) may be called from
+ *    any thread.
  */
 #ifndef DSR_H_
 #define DSR_H_

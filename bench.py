@@ -406,6 +406,10 @@ def measure_served(dsr, rt):
                                       p99_us=float(np.percentile(ok, 99)) / 1e3,
                                       sustained_regions_per_s=n / (el * 1e-9),
                                       failed=int((lat < 0).sum()))
+            # closed loop: every request due at once, so the ring stays full
+            # and the server runs at its own capacity
+            lat, el = dsr.dsr_serve_bench(rt.ctx, descs, np.zeros(n, dtype=np.int64))
+            res["capacity"] = dict(regions_per_s=n / (el * 1e-9), failed=int((lat < 0).sum()))
         finally:
             rt.serve_stop()
         served["%d_threads_%d_slab" % (shape["threads"], shape["slab_bytes"])] = res

@@ -154,3 +154,55 @@ def test_autotune_returns_fitting_shape(rt):
     g, gs = rt.fetch(b, work)
     r, rs = oracle.run_workload(work, slab_bytes=best["slab_bytes"], overflow_bytes=3 * 32768)
     assert np.array_equal(g, r)
+
+
+def _sweep_batch(sizes, teams, threads=128, seed=7):
+    """Several sweep instances in one batch: instance i has `teams` teams of
+    one fp32 frame of sizes[i] bytes, its images and outputs packed."""
+    regions, chunks = [], []
+    img_off = out_off = st = 0
+    w = threads - 32
+    for i, S in enumerate(sizes):
+        imgs = wl.normal_f32(wl.derive(seed, 30, i, S), teams * (S // 4))
+        regions.append(wl.Region(wl.PROG_SWEEP, teams, threads, 1, [S], status_index=st,
+                                 image_offset=img_off, out_offset=out_off))
+        chunks.append(imgs.view(np.uint8))
+        img_off += imgs.nbytes
+        out_off += 4 * teams * w
+        st += teams
+    return wl.Workload("sweep_batch", regions, np.concatenate(chunks), out_off, st,
+                       out_dtype="float32")
+
+
+def test_batch_sweep_streams_across_tasks():
+    """The sweep program in the persistent kernel: frames of 32 and 96 KiB
+    take the streamed fill (chunk mbarriers set up on a CTA's first streamed
+    task, their parity carried from task to task), 8 KiB frames the plain
+    bulk fill, interleaved in one CTA. Each CTA runs several tasks. Results
+    as the fp32 left-to-right sums of the oracle's order, every team OK."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1711_10413_gb300 as dsr
+    rt = dsr.Runtime(0, slab_bytes=16384, wait_timeout_ns=50_000_000)
+    try:
+        work = _sweep_batch([32768, 8192, 98304, 32768, 8192], teams=120)
+        g, gs = rt.run_batch(work, dict(threads=128, slab_bytes=98304, ctas_per_sm=1))
+        assert (gs["status"] == 0).all() and (gs["depth_final"] == 0).all()
+        assert (gs["spill_bytes"] == 0).all()
+        r, _ = oracle.run_workload(work)
+        for reg in work.regions:
+            T, W, L = reg.teams, reg.team_width, reg.frame_bytes[0] // 4
+            o0 = reg.out_offset // 4
+            got = g[o0:o0 + T * W].reshape(T, W)
+            ref = r[2 * o0: 2 * (o0 + T * W)][0::2].reshape(T, W)
+            # the same order on both sides: the fp32 sum taken left to right
+            x = work.images[reg.image_offset: reg.image_offset + T * L * 4].view(np.float32)
+            rows = (L + W - 1) // W
+            xp = np.zeros((T, rows * W), dtype=np.float32)
+            xp[:, :L] = x.reshape(T, L)
+            seq = np.add.accumulate(xp.reshape(T, rows, W), axis=1, dtype=np.float32)[:, -1, :]
+            assert np.array_equal(got, seq)
+            assert np.allclose(got, ref, rtol=1e-4, atol=1e-3)
+    finally:
+        rt.close()

@@ -296,3 +296,38 @@ def test_auto_slab_holds_every_frame(rt):
             assert _same_out(g, r)
         _assert_status_equal(gs, rs)
         assert (gs["spill_bytes"] == 0).all() and (gs["status"] == 0).all()
+
+
+# ---------------------------------------------------------------------------
+# The host-buffer path (images in and results out through pinned memory)
+# ---------------------------------------------------------------------------
+def test_run_region_host_matches_oracle(rt):
+    import torch
+
+    import paper_1711_10413_gb300 as dsr
+    cases = [(wl.nested(teams=12, threads=256, depth=3), 3264),
+             (wl.paper_scalars(9, teams=5), 4096),       # output updated in place
+             (wl.sweep(8192, teams=6), 8192)]
+    for work, slab in cases:
+        rt.configure(slab, 0, 0)
+        region = work.regions[0]
+        ib, ob, ns = dsr.dsr_region_extent(region)
+        images, out, status = rt.device_buffers(work)
+        img_h = torch.from_numpy(np.ascontiguousarray(work.images)).pin_memory()
+        out_h = torch.zeros(out.numel(), dtype=torch.int32).pin_memory()
+        if work.out_init is not None:
+            out_h[: work.out_init.size] = torch.from_numpy(work.out_init)
+        out.fill_(-1)  # stale device contents must not reach the host
+        st_h = torch.zeros(status.numel(), dtype=torch.int32).pin_memory()
+        dsr.dsr_run_region_host(rt.ctx, region, img_h, ib, out_h, ob, st_h, images, out, status)
+        g = out_h.numpy()
+        gs = st_h.numpy().view(dsr.TEAM_STATUS_DTYPE)
+        r, rs = oracle.run_workload(work, slab_bytes=slab)
+        if work.out_dtype == "float32":
+            _check_sweep(work, g.view(np.float32), r)
+        else:
+            assert _same_out(g[: ob // 4], r[: ob // 4])
+        _assert_status_equal(gs, rs)
+    with pytest.raises(dsr.DsrError) as ei:
+        dsr.dsr_run_region_host(rt.ctx, region, img_h, ib, None, ob, st_h, images, out, status)
+    assert ei.value.code == dsr.DSR_ERR_INVALID

@@ -57,7 +57,7 @@ typedef enum dsr_status {
   DSR_ERR_OVERFLOW = 2, /* a push did not fit in slab + overflow slab */
   DSR_ERR_LIFO = 3,     /* a pop named a frame that is not the top one */
   DSR_ERR_BUDGET = 4,   /* not enough pool / queue space for the request */
-  DSR_ERR_TIMEOUT = 5,  /* a bounded device-side wait ran out */
+  DSR_ERR_TIMEOUT = 5,  /* a bounded wait ran out (on the device, or a server's drain) */
   DSR_ERR_CUDA = 6      /* a CUDA runtime call failed */
 } dsr_status;
 
@@ -399,7 +399,9 @@ int32_t dsr_serve_submit(dsr_ctx *ctx, const dsr_region_desc *d, uint64_t *ticke
 int32_t dsr_serve_poll(dsr_ctx *ctx, uint64_t ticket, int32_t *status);
 
 /* Drain and stop: the server finishes every submitted request and exits;
- * blocks until it has. The rings stay for a later dsr_serve_start. */
+ * blocks until it has, for at most twice the idle timeout plus 30 s, after
+ * which it returns DSR_ERR_TIMEOUT with the server still on the GPU. The
+ * rings stay for a later dsr_serve_start. */
 int32_t dsr_serve_stop(dsr_ctx *ctx);
 
 /* Counters: requests submitted and completed, server CTAs that left on the

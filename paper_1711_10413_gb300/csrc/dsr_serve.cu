@@ -19,10 +19,10 @@
 //    exits.
 // Device workspace (caller-owned): the head of the request stream and, per
 // slot, a claim word (request sequence << 32 | next team) and counters of
-// finished teams and the worst team status. A CTA claims a team with one
-// 64-bit atomic add on the claim word and keeps it only when the sequence
-// half still names the request it read, so a slot reused for a later
-// request is never mistaken for an earlier one.
+// finished teams and the worst team status. A CTA claims a run of teams with
+// a 64-bit compare-and-swap on the claim word, which succeeds only while
+// the sequence half still names the request it read, so a slot reused for a
+// later request is never mistaken for an earlier one.
 // One CTA, the doorbell, reads host memory: it copies every new request's
 // descriptor into a device-memory ring and then the tail and the stop flag
 // into device memory, where the other CTAs poll with backoff; the other CTAs
@@ -666,7 +666,18 @@ extern "C" int32_t dsr_serve_stop(dsr_ctx *ctx) {
   if (!ctx || !ctx->serve) return DSR_OK;
   dsr_serve_state *sv = ctx->serve;
   __atomic_store_n(&sv->hs->stop, 1ull, __ATOMIC_RELEASE);
-  cudaError_t e = cudaStreamSynchronize(sv->stream);
+  // Every CTA leaves once the stop is seen and nothing is left to claim, or
+  // after its idle timeout; wait for that, but not without end: a server
+  // still running well past its idle timeout is reported, not waited on.
+  const uint64_t idle = sv->cfg.idle_timeout_ns ? sv->cfg.idle_timeout_ns : 2000000000ull;
+  const uint64_t deadline = now_ns() + 2 * idle + 30000000000ull;
+  cudaError_t e;
+  while ((e = cudaStreamQuery(sv->stream)) == cudaErrorNotReady) {
+    if (now_ns() > deadline)
+      return dsr_fail(ctx, DSR_ERR_TIMEOUT, "server did not drain within %.0f s of the stop",
+                      (2 * idle + 30000000000ull) * 1e-9);
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
   sv->running = false;
   __atomic_store_n(&sv->hs->stop, 0ull, __ATOMIC_RELEASE);
   drain_completions(sv);

@@ -1,4 +1,5 @@
-"""Running independent region instances on several GPUs, one process each.
+"""Running independent region instances on several GPUs, one process each:
+batches split by instance, served requests routed by load.
 
 Teams share nothing across teams (each has its own stack, Sec. 4: a team
 is a thread block), and region instances share nothing across instances.
@@ -46,6 +47,27 @@ def balanced_ranges(weights: Sequence[int], world: int) -> List[Tuple[int, int]]
             start = ranges[-1][1] if ranges else 0
             ranges.append((start, start))
     return ranges
+
+
+def route_requests(weights: Sequence[int], world: int) -> np.ndarray:
+    """Serving on several GPUs: the rank (GPU) of each request, in arrival
+    order, each to the rank with the least weight (teams, say) routed so far,
+    ties to the lowest rank. The routing depends on the requests alone, so
+    every rank computes the same one and keeps its own requests, with no
+    message between ranks; every rank then serves its requests with its own
+    server."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    w = np.asarray(weights, dtype=np.int64)
+    if (w < 0).any():
+        raise ValueError("weights must be non-negative")
+    load = np.zeros(world, dtype=np.int64)
+    rank = np.empty(len(w), dtype=np.int64)
+    for i, x in enumerate(w.tolist()):
+        r = int(np.argmin(load))
+        rank[i] = r
+        load[r] += x
+    return rank
 
 
 def _scalar_tensor(value: float, dist):

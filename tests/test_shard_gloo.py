@@ -90,3 +90,50 @@ def test_balanced_ranges_edge_cases():
     with pytest.raises(ValueError):
         shard.balanced_ranges([1, 2], 0)
     assert shard.max_over_ranks(3.0) == 3.0 and shard.sum_over_ranks(2.0) == 2.0
+
+
+def _serve_rank_main(rank, world, port, result_path):
+    """Each rank serves the requests routed to it (through the oracle here);
+    rank 0 gathers every request's result, which must equal one run of all
+    the requests."""
+    import torch.distributed as dist
+
+    import oracle
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        teams = wl.hetero_shapes(N_INST, max_teams=MAX_TEAMS, max_frame=MAX_FRAME)[0]
+        routed = shard.route_requests(teams, world)
+        ids = np.nonzero(routed == rank)[0]
+        work = wl.hetero(N_INST, max_teams=MAX_TEAMS, max_frame=MAX_FRAME, instances=ids)
+        out, status = oracle.run_workload(work, SLAB, OVF)
+        merged = shard.gather_to_rank0(_instance_results(work, out, status, ids), dist)
+        if rank == 0:
+            full = wl.hetero(N_INST, max_teams=MAX_TEAMS, max_frame=MAX_FRAME)
+            fo, fs = oracle.run_workload(full, SLAB, OVF)
+            want = _instance_results(full, fo, fs, np.arange(N_INST))
+            ok = (sorted(merged) == list(range(N_INST))
+                  and all(np.array_equal(merged[i], want[i]) for i in range(N_INST)))
+            with open(result_path, "w") as f:
+                f.write("ok" if ok else "mismatch")
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_routed_requests_equal_whole(tmp_path):
+    import torch.multiprocessing as mp
+    path = str(tmp_path / "served.txt")
+    mp.spawn(_serve_rank_main, args=(2, _free_port(), path), nprocs=2, join=True)
+    assert open(path).read() == "ok"
+
+
+@pytest.mark.parametrize("world", [1, 2, 4])
+def test_route_requests_balances_load(world):
+    teams = wl.hetero_shapes(1000)[0]
+    rank = shard.route_requests(teams, world)
+    assert rank.min() >= 0 and rank.max() < world and len(rank) == 1000
+    loads = [int(teams[rank == r].sum()) for r in range(world)]
+    # greedy least-loaded: no rank ends more than one request above another
+    assert max(loads) - min(loads) <= int(teams.max())
+    assert (shard.route_requests(teams, world) == rank).all()  # the same on every rank

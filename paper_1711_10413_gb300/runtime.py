@@ -4,8 +4,6 @@ Argument marshalling only: every call goes straight to the C ABI.
 """
 from __future__ import annotations
 
-from typing import Optional
-
 import numpy as np
 
 from . import (TEAM_STATUS_DTYPE, dsr_autotune, dsr_batch_count, dsr_batch_errors,

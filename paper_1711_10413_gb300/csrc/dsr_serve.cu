@@ -165,38 +165,69 @@ __device__ __forceinline__ bool claim_in(const ServeArgs &a, unsigned long long 
 
 // Claim teams of a submitted request (master warp). Returns false when
 // no team is available now. The CTA first tries the request it ran last
-// (`hint`), then looks at the kWindow oldest requests in flight, starting at
-// one that depends on its block index, so claims spread over the window.
-constexpr uint32_t kWindow = 32;
+// (`hint`). Then the warp looks at the kWindow oldest requests in flight at
+// once, one per lane, so their claim words are read in one round trip
+// rather than one after another; lane 0 tries those with teams left,
+// starting at one that depends on its block index so that claims spread
+// over the window, and moves the head past every leading request that has
+// no team left to hand out.
+constexpr uint32_t kWindow = 32;  // one request per lane
 
 __device__ __forceinline__ bool claim(const ServeArgs &a, unsigned long long hint,
                                       unsigned long long *seq, uint32_t *team, uint32_t *count) {
+  const uint32_t lane = lane_id();
   unsigned long long out_seq = 0;
   uint32_t out_team = 0, out_count = 0, got = 0;
-  if (lane_id() == 0) {
+  if (lane == 0 && hint != ~0ull) {
     bool adv;
-    if (hint != ~0ull && claim_in(a, hint, &out_team, &out_count, &adv)) {
+    if (claim_in(a, hint, &out_team, &out_count, &adv)) {
       got = 1;
       out_seq = hint;
     }
-    for (int tries = 0; tries < 8 && !got; ++tries) {
-      const unsigned long long h = ld_relaxed_gpu(&a.ws->head);
-      const unsigned long long tail = ld_acquire_gpu(&a.ws->tail);
-      if (h >= tail) break;
-      const uint32_t n = static_cast<uint32_t>(min(tail - h, static_cast<unsigned long long>(kWindow)));
-      const uint32_t start = (blockIdx.x * 7u + static_cast<uint32_t>(tries)) % n;
-      for (uint32_t j = 0; j < n && !got; ++j) {
-        const unsigned long long r = h + (start + j) % n;
-        if (claim_in(a, r, &out_team, &out_count, &adv)) {
+  }
+  got = __shfl_sync(0xffffffffu, got, 0);
+  for (uint32_t tries = 0; tries < 8 && !got; ++tries) {
+    unsigned long long h = 0, tail = 0;
+    if (lane == 0) {
+      h = ld_relaxed_gpu(&a.ws->head);
+      tail = ld_acquire_gpu(&a.ws->tail);  // the doorbell's slot writes before it
+    }
+    h = __shfl_sync(0xffffffffu, h, 0);
+    tail = __shfl_sync(0xffffffffu, tail, 0);
+    __syncwarp();  // orders lane 0's acquire before the other lanes' slot reads
+    if (h >= tail) break;
+    const uint32_t n = static_cast<uint32_t>(min(tail - h, static_cast<unsigned long long>(kWindow)));
+    bool avail = false, spent = false;
+    if (lane < n) {
+      const unsigned long long r = h + lane;
+      const SlotState *st = a.slots + static_cast<uint32_t>(r % a.capacity);
+      const uint32_t T = *reinterpret_cast<volatile const unsigned int *>(&st->teams);
+      const unsigned long long w = ld_relaxed_gpu(&st->claim);
+      // teams left when the slot still holds r and not all are handed out;
+      // otherwise r has none left (all handed out, or r done and its slot
+      // passed on to a later request)
+      avail = (w >> 32) == (r & 0xffffffffull) && static_cast<uint32_t>(w) < T;
+      spent = !avail;
+    }
+    const uint32_t avail_m = __ballot_sync(0xffffffffu, avail);
+    const uint32_t spent_m = __ballot_sync(0xffffffffu, spent);
+    if (lane == 0) {
+      const uint32_t lead = ~spent_m ? static_cast<uint32_t>(__ffs(~spent_m)) - 1u : 32u;
+      if (lead) atomicCAS(&a.ws->head, h, h + lead);  // the head passes spent requests
+      const uint32_t start = (blockIdx.x * 7u + tries) % n;
+      uint32_t m = start ? (avail_m >> start) | (avail_m << (32u - start)) : avail_m;
+      while (m && !got) {
+        const uint32_t j = (static_cast<uint32_t>(__ffs(m)) - 1u + start) & 31u;
+        m &= m - 1u;
+        bool adv;
+        if (claim_in(a, h + j, &out_team, &out_count, &adv)) {
           got = 1;
-          out_seq = r;
-        } else if (adv && r == h) {
-          atomicCAS(&a.ws->head, h, h + 1);  // the head may pass a handed-out request
+          out_seq = h + j;
         }
       }
     }
+    got = __shfl_sync(0xffffffffu, got, 0);
   }
-  got = __shfl_sync(0xffffffffu, got, 0);
   *seq = __shfl_sync(0xffffffffu, out_seq, 0);
   *team = __shfl_sync(0xffffffffu, out_team, 0);
   *count = __shfl_sync(0xffffffffu, out_count, 0);

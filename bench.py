@@ -50,10 +50,10 @@ import workloads as wl  # noqa: E402
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
 # CTA shapes of the device-resident server (threads per CTA, shared slab
-# bytes): the two best of 96/8 KB, 128/16 KB, 256/16 KB and 512/32 KB in a
-# sweep at 100k to 1M requests/s on the hetero distribution. 256 threads
-# gives the lower latency, 128 the higher saturation throughput.
-SERVE_SHAPES = [dict(threads=256, slab_bytes=16384), dict(threads=128, slab_bytes=16384)]
+# bytes), from sweeps of 96 to 512 threads and 8 to 32 KiB slabs on the
+# hetero distribution: 256 threads gives the lowest latency, 128 threads
+# with 8 KiB slabs (the most resident CTAs) the highest capacity.
+SERVE_SHAPES = [dict(threads=256, slab_bytes=16384), dict(threads=128, slab_bytes=8192)]
 
 # DRAM traffic (read + write bytes per launch) of the plain nested kernel from
 # one ncu capture (profiles/nested_1024x256_d3_full.md), keyed by a hash of

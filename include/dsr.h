@@ -240,8 +240,12 @@ int32_t dsr_region_occupancy(dsr_ctx *ctx, const dsr_region_desc *d, dsr_occupan
  * records, of which teams d->status_index .. + d->teams - 1 are written.
  * The descriptor is checked against these sizes before anything launches.
  * Requires dsr_stack_init; d->teams <= the max_teams given there when an
- * overflow slab is configured. Asynchronous. Errors: DSR_ERR_INVALID,
- * DSR_ERR_BUDGET, DSR_ERR_CUDA (launch failure). */
+ * overflow slab is configured. Asynchronous. The launch allows
+ * programmatic stream serialisation: its CTAs may be placed while the kernel
+ * before it in the stream drains, but none of its threads touches global
+ * memory before that kernel has completed, so stream order holds for every
+ * buffer. Errors: DSR_ERR_INVALID, DSR_ERR_BUDGET, DSR_ERR_CUDA (launch
+ * failure). */
 int32_t dsr_launch_region(dsr_ctx *ctx, const dsr_region_desc *d, const void *images_dev,
                           uint64_t image_bytes, void *out_dev, uint64_t out_bytes,
                           dsr_team_status *status_dev, uint64_t n_status, void *stream);

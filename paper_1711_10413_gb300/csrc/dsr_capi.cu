@@ -33,7 +33,9 @@ __global__ void __launch_bounds__(MAXT, MINB)
   e.images = images;
   e.out = out;
   e.team = blockIdx.x;
+  if (threadIdx.x == 0) signal_dependents();
   if (threadIdx.x < team_workers()) {
+    wait_prerequisites();
     worker_loop<P>(e);
     return;
   }
@@ -41,6 +43,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
   team_setup(s, slab_bytes,
              ovf_per_team ? pool + static_cast<uint64_t>(blockIdx.x) * ovf_per_team : nullptr,
              ovf_per_team, timeout_ns, true);
+  wait_prerequisites();  // the set-up above touches shared memory only
   P::master(e, s);
   terminate_workers();
   team_report(e, s, st);
@@ -322,10 +325,24 @@ int32_t dsr_launch_plain(dsr_ctx *ctx, const dsr_region_desc *d, const void *ima
   const uint32_t block = d->threads > 32u ? d->threads : 64u;
   KernelFn k = plain_kernel_for(d->program, block);
   const uint32_t slab = dsr_plain_slab(ctx, d);
-  k<<<d->teams, block, kCtrlBytes + slab, s>>>(
-      *d, static_cast<const uint8_t *>(images_dev), static_cast<uint8_t *>(out_dev), status_dev,
-      ctx->pool, ctx->ovf_per_team, slab, ctx->timeout_ns);
-  cudaError_t e = cudaGetLastError();
+  // programmatic stream serialisation: this grid may be dispatched while the
+  // kernel before it in the stream drains (its threads wait for that kernel
+  // before touching global memory); consecutive regions overlap a launch's
+  // CTA placement with the previous region's tail
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(d->teams);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = kCtrlBytes + slab;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(
+      &cfg, k, *d, static_cast<const uint8_t *>(images_dev), static_cast<uint8_t *>(out_dev),
+      status_dev, ctx->pool, ctx->ovf_per_team, slab, ctx->timeout_ns);
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "plain launch");
   return DSR_OK;
 }

@@ -229,6 +229,19 @@ struct Stack {
 
 // Team setup (master warp): the stack starts empty. `first` initialises the
 // fill mbarrier (once per CTA).
+// Programmatic dependent launch (an attribute of the plain form's launch):
+// the next grid in the stream may be dispatched once every CTA of this grid
+// has signalled, so its CTAs are placed and set up while this grid drains;
+// every thread of a grid waits for the grids before it to complete, their
+// memory visible, before its first global-memory access. In a grid launched
+// without the attribute both are no-ops.
+__device__ __forceinline__ void signal_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void wait_prerequisites() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __device__ __forceinline__ void team_setup(Stack &s, uint32_t slab_bytes, uint8_t *ovf,
                                            uint64_t ovf_bytes, uint64_t timeout_ns, bool first) {
   Ctrl *c = ctrl();

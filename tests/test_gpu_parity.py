@@ -331,3 +331,39 @@ def test_run_region_host_matches_oracle(rt):
     with pytest.raises(dsr.DsrError) as ei:
         dsr.dsr_run_region_host(rt.ctx, region, img_h, ib, None, ob, st_h, images, out, status)
     assert ei.value.code == dsr.DSR_ERR_INVALID
+
+
+def test_region_reads_the_previous_regions_output(rt):
+    """Back to back in one stream with no synchronisation between them, region
+    B's init images are region A's output. The plain launch lets B's CTAs be
+    placed while A still runs (A's 512 teams leave most of the GPU's CTA
+    slots free), so B is right only if none of B's threads reads global
+    memory before A has completed. Six pairs on fresh buffers, all launched
+    before one synchronisation; both regions checked against the oracle."""
+    import torch
+    import paper_1711_10413_gb300 as dsr
+    T = 512
+    a = wl.nested(teams=T, threads=256, depth=3, elems_per_team=4096, seed=11)
+    ref_a, ref_as = oracle.run_workload(a, slab_bytes=3264)
+    b = wl.nested(teams=T, threads=256, depth=3, elems_per_team=4096, seed=12)
+    assert a.out_bytes >= len(b.images)
+    b_on_a = wl.Workload("nested_on_a", b.regions, np.ascontiguousarray(ref_a.view(np.uint8)),
+                         b.out_bytes, b.n_status)
+    ref_b, ref_bs = oracle.run_workload(b_on_a, slab_bytes=3264)
+    _configure(rt, 3264)
+    img_a, _, _ = rt.device_buffers(a)
+    pairs = []
+    for _ in range(6):
+        out_a = torch.empty(a.out_bytes // 4, dtype=torch.int32, device="cuda")
+        st_a = torch.zeros(a.n_status * 8, dtype=torch.int32, device="cuda")
+        out_b = torch.empty(b.out_bytes // 4, dtype=torch.int32, device="cuda")
+        st_b = torch.zeros(b.n_status * 8, dtype=torch.int32, device="cuda")
+        rt.launch(a.regions[0], img_a, out_a, st_a)
+        rt.launch(b.regions[0], out_a.view(torch.uint8), out_b, st_b)
+        pairs.append((out_a, st_a, out_b, st_b))
+    torch.cuda.synchronize()
+    for out_a, st_a, out_b, st_b in pairs:
+        assert np.array_equal(out_a.cpu().numpy(), ref_a)
+        _assert_status_equal(st_a.cpu().numpy().view(dsr.TEAM_STATUS_DTYPE), ref_as)
+        assert np.array_equal(out_b.cpu().numpy(), ref_b)
+        _assert_status_equal(st_b.cpu().numpy().view(dsr.TEAM_STATUS_DTYPE), ref_bs)

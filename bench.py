@@ -610,11 +610,49 @@ def main():
     ms_flushed = shard.max_over_ranks(ms_flushed, dist)
     del sets
 
-    # e2e: the same region from pinned host memory through the C ABI
-    img_h = torch.from_numpy(np.ascontiguousarray(work.images)).pin_memory()
-    out_h = torch.empty(out.numel(), dtype=torch.int32).pin_memory()
-    st_h = torch.empty(status.numel(), dtype=torch.int32).pin_memory()
+    # e2e through the C ABI from pinned host memory: every step uploads its
+    # images, runs the region, downloads its output and statuses, and the
+    # host checks that step's statuses before the slot is used again. Steps
+    # alternate between two streams, each with its own device and host
+    # buffers, so one step's download overlaps the next step's upload and
+    # kernel (dsr_enqueue_region_host). The one-step-at-a-time call
+    # (dsr_run_region_host, synchronised every step) is timed beside it.
     ib, ob, _ = dsr.dsr_region_extent(region)
+    img_h = torch.from_numpy(np.ascontiguousarray(work.images)).pin_memory()
+    e2e_streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    e2e_dev = [(images, out, status), rt.device_buffers(work)]
+    e2e_host = [(torch.empty(out.numel(), dtype=torch.int32).pin_memory(),
+                 torch.empty(status.numel(), dtype=torch.int32).pin_memory()) for _ in range(2)]
+    e2e_done = [torch.cuda.Event(), torch.cuda.Event()]
+    e2e_bad = [0]
+    torch.cuda.synchronize()
+
+    def e2e_run(n):
+        for i in range(n + 2):
+            k = i % 2
+            if i >= 2:   # step i - 2 used this slot: wait for it and read its statuses
+                e2e_done[k].synchronize()
+                st = e2e_host[k][1].numpy().view(dsr.TEAM_STATUS_DTYPE)
+                e2e_bad[0] += int((st["status"] != 0).sum())
+            if i < n:
+                im, o, st_d = e2e_dev[k]
+                oh, sh = e2e_host[k]
+                dsr.dsr_enqueue_region_host(rt.ctx, region, img_h, ib, oh, ob, sh, im, o, st_d,
+                                            e2e_streams[k])
+                e2e_done[k].record(e2e_streams[k])
+
+    e2e_run(args.warmup)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    e2e_run(args.steps)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t1) / args.steps
+    e2e_s = shard.max_over_ranks(e2e_s, dist)
+    e2e_agree = bool(np.array_equal(e2e_host[0][0].numpy(), out.cpu().numpy()))
+
+    out_h, st_h = e2e_host[0]
 
     def e2e_step():
         dsr.dsr_run_region_host(rt.ctx, region, img_h, ib, out_h, ob, st_h, images, out,
@@ -622,15 +660,12 @@ def main():
 
     for _ in range(args.warmup):
         e2e_step()
-    if dist:
-        dist.barrier()
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     for _ in range(args.steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t1) / args.steps
-    e2e_s = shard.max_over_ranks(e2e_s, dist)
+    e2e_serial_s = shard.max_over_ranks((time.perf_counter() - t1) / args.steps, dist)
 
     if rank != 0:
         if dist:
@@ -653,7 +688,10 @@ def main():
                       frac=achieved / peaks["hbm_gbs"], traffic=_traffic(),
                       peak_source=peaks["source"], algorithmic_bytes=algo_bytes),
         e2e=dict(value=regions_done / e2e_s, unit="regions/s", h2d_bytes_per_step=int(ib),
-                 d2h_bytes_per_step=int(ob + 32 * region.teams)),
+                 d2h_bytes_per_step=int(ob + 32 * region.teams),
+                 how="dsr_enqueue_region_host, steps alternating over two streams",
+                 bad_team_status=e2e_bad[0], output_agrees=e2e_agree,
+                 one_step_at_a_time=regions_done / e2e_serial_s),
         gpu_launches=args.steps,
         bracket_ms_per_step=1000.0 * bracket_s / args.steps,
         bad_team_status=bad_status,

@@ -260,6 +260,19 @@ int32_t dsr_run_region_host(dsr_ctx *ctx, const dsr_region_desc *d, const void *
                             dsr_team_status *status_host, void *images_dev, void *out_dev,
                             dsr_team_status *status_dev, void *stream);
 
+/* dsr_run_region_host without the final synchronisation: the upload, the
+ * launch and the downloads are enqueued on `stream` and the call returns.
+ * The host buffers must be pinned (so the copies are asynchronous) and must
+ * not be touched until the stream has passed the downloads. Steps enqueued
+ * on two streams, each with its own device and host buffers, overlap one
+ * step's download with the next step's upload and kernel. Same arguments
+ * and errors as dsr_run_region_host, except that a failure of the copies
+ * or the kernel surfaces at the caller's synchronisation. */
+int32_t dsr_enqueue_region_host(dsr_ctx *ctx, const dsr_region_desc *d, const void *images_host,
+                                uint64_t image_bytes, void *out_host, uint64_t out_bytes,
+                                dsr_team_status *status_host, void *images_dev, void *out_dev,
+                                dsr_team_status *status_dev, void *stream);
+
 /* ---- batched launch: many instances, one persistent kernel -------------- */
 
 /* CTA shape of the persistent kernel. Teams of any width run on it: a region

@@ -114,6 +114,8 @@ def _declare(L):
                                      _vp]),
         "dsr_run_region_host": (_i32, [_vp, P(dsr_region_desc), _vp, _u64, _vp, _u64, _vp,
                                        _vp, _vp, _vp, _vp]),
+        "dsr_enqueue_region_host": (_i32, [_vp, P(dsr_region_desc), _vp, _u64, _vp, _u64, _vp,
+                                           _vp, _vp, _vp, _vp]),
         "dsr_batch_workspace_bytes": (_u64, [_u32, _u64]),
         "dsr_batch_count": (_i32, [_vp, _u32, _u64, _u64, _u64, P(_u64)]),
         "dsr_launch_batch": (_i32, [_vp, _vp, _u32, _u32, _u64, _vp, _u64, _vp, _u64, _vp, _u64,
@@ -161,7 +163,8 @@ def exported_symbols():
     return ["dsr_create", "dsr_destroy", "dsr_last_error_string", "dsr_stack_init",
             "dsr_validate_region", "dsr_region_extent", "dsr_footprint_model",
             "dsr_region_occupancy", "dsr_region_footprint",
-            "dsr_launch_region", "dsr_run_region_host", "dsr_batch_workspace_bytes",
+            "dsr_launch_region", "dsr_run_region_host", "dsr_enqueue_region_host",
+            "dsr_batch_workspace_bytes",
             "dsr_batch_count", "dsr_launch_batch", "dsr_batch_errors", "dsr_autotune",
             "dsr_launch_regions", "dsr_launch_batch_static", "dsr_batch_static_capacity",
             "dsr_serve_workspace_bytes", "dsr_serve_start",
@@ -309,6 +312,17 @@ def dsr_run_region_host(ctx: int, region, images_host, image_bytes: int, out_hos
                                      _ptr(out_host), out_bytes, _ptr(status_host),
                                      _ptr(images_dev), _ptr(out_dev), _ptr(status_dev),
                                      _stream(stream)), ctx)
+
+
+def dsr_enqueue_region_host(ctx: int, region, images_host, image_bytes: int, out_host,
+                            out_bytes: int, status_host, images_dev, out_dev, status_dev,
+                            stream=None) -> None:
+    """dsr_run_region_host without the synchronisation (pinned host buffers)."""
+    d = pack_desc(region)
+    _check(lib().dsr_enqueue_region_host(ctx, ctypes.byref(d), _ptr(images_host), image_bytes,
+                                         _ptr(out_host), out_bytes, _ptr(status_host),
+                                         _ptr(images_dev), _ptr(out_dev), _ptr(status_dev),
+                                         _stream(stream)), ctx)
 
 
 def _tuning(t):

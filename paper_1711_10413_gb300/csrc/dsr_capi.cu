@@ -405,12 +405,12 @@ extern "C" int32_t dsr_region_occupancy(dsr_ctx *ctx, const dsr_region_desc *d,
   return DSR_OK;
 }
 
-extern "C" int32_t dsr_run_region_host(dsr_ctx *ctx, const dsr_region_desc *d,
-                                       const void *images_host, uint64_t image_bytes,
-                                       void *out_host, uint64_t out_bytes,
-                                       dsr_team_status *status_host, void *images_dev,
-                                       void *out_dev, dsr_team_status *status_dev,
-                                       void *stream) {
+extern "C" int32_t dsr_enqueue_region_host(dsr_ctx *ctx, const dsr_region_desc *d,
+                                           const void *images_host, uint64_t image_bytes,
+                                           void *out_host, uint64_t out_bytes,
+                                           dsr_team_status *status_host, void *images_dev,
+                                           void *out_dev, dsr_team_status *status_dev,
+                                           void *stream) {
   int32_t rc = check_launch(ctx, d, out_dev, status_dev);
   if (rc != DSR_OK) return rc;
   if (!out_host || !status_host) return dsr_fail(ctx, DSR_ERR_INVALID, "null host buffers");
@@ -437,6 +437,19 @@ extern "C" int32_t dsr_run_region_host(dsr_ctx *ctx, const dsr_region_desc *d,
                            sizeof(dsr_team_status) * d->teams, cudaMemcpyDeviceToHost, s)) !=
           cudaSuccess)
     return dsr_cuda_fail(ctx, e, "download");
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return dsr_cuda_fail(ctx, e, "sync");
+  return DSR_OK;
+}
+
+extern "C" int32_t dsr_run_region_host(dsr_ctx *ctx, const dsr_region_desc *d,
+                                       const void *images_host, uint64_t image_bytes,
+                                       void *out_host, uint64_t out_bytes,
+                                       dsr_team_status *status_host, void *images_dev,
+                                       void *out_dev, dsr_team_status *status_dev,
+                                       void *stream) {
+  int32_t rc = dsr_enqueue_region_host(ctx, d, images_host, image_bytes, out_host, out_bytes,
+                                       status_host, images_dev, out_dev, status_dev, stream);
+  if (rc != DSR_OK) return rc;
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "sync");
   return DSR_OK;
 }

@@ -333,6 +333,39 @@ def test_run_region_host_matches_oracle(rt):
     assert ei.value.code == dsr.DSR_ERR_INVALID
 
 
+def test_enqueue_region_host_pipelines_on_two_streams(rt):
+    """Eight steps enqueued on two streams without synchronisation, each
+    step with its own input images (a different seed), device buffers and
+    pinned host outputs; a slot's device buffers are reused two steps later
+    on the same stream. After one synchronisation every host output and
+    status record equals the oracle's for that step's inputs."""
+    import torch
+
+    import paper_1711_10413_gb300 as dsr
+    T, slab = 256, 3264
+    rt.configure(slab, 0, 0)
+    works = [wl.nested(teams=T, threads=256, depth=3, seed=100 + i) for i in range(8)]
+    region = works[0].regions[0]
+    ib, ob, _ = dsr.dsr_region_extent(region)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    slots = [rt.device_buffers(works[0]) for _ in streams]
+    torch.cuda.synchronize()  # the slots' set-up ran on the default stream
+    host = []
+    for i, work in enumerate(works):
+        img_h = torch.from_numpy(np.ascontiguousarray(work.images)).pin_memory()
+        out_h = torch.full((ob // 4,), -1, dtype=torch.int32).pin_memory()
+        st_h = torch.zeros(T * 8, dtype=torch.int32).pin_memory()
+        images, out, status = slots[i % 2]
+        dsr.dsr_enqueue_region_host(rt.ctx, region, img_h, ib, out_h, ob, st_h, images, out,
+                                    status, streams[i % 2].cuda_stream)
+        host.append((img_h, out_h, st_h))
+    torch.cuda.synchronize()
+    for work, (_, out_h, st_h) in zip(works, host):
+        r, rs = oracle.run_workload(work, slab_bytes=slab)
+        assert np.array_equal(out_h.numpy(), r[: ob // 4])
+        _assert_status_equal(st_h.numpy().view(dsr.TEAM_STATUS_DTYPE), rs)
+
+
 def test_region_reads_the_previous_regions_output(rt):
     """Back to back in one stream with no synchronisation between them, region
     B's init images are region A's output. The plain launch lets B's CTAs be

@@ -164,6 +164,33 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle timing (bounded sample of the same workload)
 # ---------------------------------------------------------------------------
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (x86: model name; Arm: the
+    implementer and part codes, 0x41/0xd4f being Neoverse V2, Grace's core)."""
+    import platform
+    name, impl, part = "", "", ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                k, v = k.strip(), v.strip()
+                if k == "model name" and not name:
+                    name = v
+                elif k == "CPU implementer" and not impl:
+                    impl = v
+                elif k == "CPU part" and not part:
+                    part = v
+    except OSError:
+        pass
+    if name:
+        return name
+    if impl or part:
+        known = {("0x41", "0xd4f"): "Arm Neoverse V2"}
+        return "%s (implementer %s, part %s)" % (known.get((impl, part), platform.machine()),
+                                                impl, part)
+    return platform.machine()
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -211,6 +238,7 @@ def time_oracle(work, slab, ovf, budget_s: float = 10.0, threads: int = 1):
     teams_done = sum(done)
     regions = teams_done / r.teams
     return dict(value=regions / dt, unit="regions/s", cores=threads, kind="oracle",
+                cpu=cpu_model(),
                 sample="%d teams of the workload (%.2f regions) in %.1f s, %d thread%s"
                        % (teams_done, regions, dt, threads, "" if threads == 1 else "s"))
 
@@ -519,7 +547,8 @@ def main():
                     e2e=dict(value=v, unit="regions/s", h2d_bytes_per_step=0,
                              d2h_bytes_per_step=0),
                     cpu_baseline=dict(value=v, unit="regions/s", cores=samples[-1]["cores"],
-                                      kind="oracle", sample=samples[-1]["sample"]))
+                                      kind="oracle", cpu=samples[-1]["cpu"],
+                                      sample=samples[-1]["sample"]))
         print(json.dumps(line))
         return
 

@@ -368,17 +368,35 @@ struct ProgSweep {
                               uint32_t streamed) {
     const float *arr = reinterpret_cast<const float *>(ctrl()->frames[0].ptr);
     const uint32_t L = ctrl()->frames[0].bytes / 4u;
+    // a spilled frame is read from L2/HBM: twice the loads in flight
+    const float acc = __isShared(arr) ? strided_sum<16>(arr, L, tid, n, streamed)
+                                      : strided_sum<32>(arr, L, tid, n, streamed);
+    reinterpret_cast<float *>(e.out + e.d->out_offset)[e.team * n + tid] = acc;
+  }
+
+  // arr[tid] + arr[tid + n] + ... left to right in fp32. Rounds of kB loads
+  // in flight (then of 4, then single loads), each followed by its
+  // additions one by one in index order: the sum is the same left-to-right
+  // fp32 sum, but the memory latency (shared memory, or L2/HBM for a
+  // spilled frame) is paid once per round instead of once per element.
+  template <uint32_t kB>
+  __device__ static float strided_sum(const float *arr, uint32_t L, uint32_t tid, uint32_t n,
+                                      uint32_t streamed) {
     float acc = 0.0f;
     uint32_t i = tid;
     // bytes of a streamed frame known to have landed (all of any other)
     uint32_t ready = streamed ? 0u : 0xffffffffu;
-    // Sixteen loads in flight, then their additions one by one in index
-    // order: the sum is the same left-to-right fp32 sum, but the memory
-    // latency (shared memory, or L2/HBM for a spilled frame) is paid once
-    // per sixteen elements instead of once per element.
-    constexpr uint32_t kB = 16;
+    sum_rounds<kB>(arr, L, n, i, acc, ready);
+    sum_rounds<4>(arr, L, n, i, acc, ready);
+    sum_rounds<1>(arr, L, n, i, acc, ready);
+    return acc;
+  }
+
+  template <uint32_t kB>
+  __device__ static void sum_rounds(const float *arr, uint32_t L, uint32_t n, uint32_t &i,
+                                    float &acc, uint32_t &ready) {
     for (; i + (kB - 1u) * n < L; i += kB * n) {
-      const uint32_t end = 4u * (i + (kB - 1u) * n) + 4u;  // past the batch's last byte
+      const uint32_t end = 4u * (i + (kB - 1u) * n) + 4u;  // past the round's last byte
       if (end > ready) ready = stream_ready(end, ready);
       float x[kB];
 #pragma unroll
@@ -386,11 +404,6 @@ struct ProgSweep {
 #pragma unroll
       for (uint32_t u = 0; u < kB; ++u) acc = __fadd_rn(acc, x[u]);
     }
-    for (; i < L; i += n) {
-      if (4u * i + 4u > ready) ready = stream_ready(4u * i + 4u, ready);
-      acc = __fadd_rn(acc, arr[i]);
-    }
-    reinterpret_cast<float *>(e.out + e.d->out_offset)[e.team * n + tid] = acc;
   }
 };
 

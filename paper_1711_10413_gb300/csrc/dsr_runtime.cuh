@@ -358,11 +358,35 @@ __device__ __forceinline__ void pop_top(Stack &s) {
   s.bits = (s.bits & ~0xffu) | static_cast<uint32_t>(keep);
 }
 
+// kDepth 16-byte loads in flight for one thread's vectors i, i + nthr, ...
+// below nv, then their stores XOR key; returns the first vector not copied.
+template <uint32_t kDepth>
+__device__ __forceinline__ uint32_t copy_xor_batches(uint4 *dv, const uint4 *sv, uint32_t nv,
+                                                     uint32_t key, uint32_t i, uint32_t nthr) {
+  for (; i + (kDepth - 1u) * nthr < nv; i += kDepth * nthr) {
+    uint4 x[kDepth];
+#pragma unroll
+    for (uint32_t u = 0; u < kDepth; ++u) x[u] = __ldg(sv + i + u * nthr);
+#pragma unroll
+    for (uint32_t u = 0; u < kDepth; ++u) {
+      x[u].x ^= key;
+      x[u].y ^= key;
+      x[u].z ^= key;
+      x[u].w ^= key;
+      dv[i + u * nthr] = x[u];
+    }
+  }
+  return i;
+}
+
 // dst[w] = src[w] ^ key for the words of `bytes` (a multiple of 4), split
 // over `nthr` threads (this one is `idx`); 16-byte vectors when aligned.
-// kBatch keeps four vector loads in flight per thread (16 more registers;
-// off in kernels held to 32 registers).
-template <bool kBatch>
+// Up to kDepth vector loads are in flight per thread before their stores:
+// a copy between two global buffers is bound by the bytes in flight. Rounds
+// of kDepth, then of 4, then single vectors, so that frames too small for a
+// full round of kDepth still keep several loads in flight. Each step of
+// depth costs four registers (1 in kernels held to 32).
+template <uint32_t kDepth>
 __device__ __forceinline__ void copy_xor(uint8_t *dst, const uint8_t *src, uint32_t bytes,
                                          uint32_t key, uint32_t idx, uint32_t nthr) {
   uint32_t w0 = 0;
@@ -371,28 +395,9 @@ __device__ __forceinline__ void copy_xor(uint8_t *dst, const uint8_t *src, uint3
     const uint4 *sv = reinterpret_cast<const uint4 *>(src);
     uint4 *dv = reinterpret_cast<uint4 *>(dst);
     uint32_t i = idx;
-    // four 16-byte loads in flight before their stores
-    for (; kBatch && i + 3u * nthr < nv; i += 4u * nthr) {
-      uint4 x[4];
-#pragma unroll
-      for (uint32_t u = 0; u < 4u; ++u) x[u] = __ldg(sv + i + u * nthr);
-#pragma unroll
-      for (uint32_t u = 0; u < 4u; ++u) {
-        x[u].x ^= key;
-        x[u].y ^= key;
-        x[u].z ^= key;
-        x[u].w ^= key;
-        dv[i + u * nthr] = x[u];
-      }
-    }
-    for (; i < nv; i += nthr) {
-      uint4 x = __ldg(sv + i);
-      x.x ^= key;
-      x.y ^= key;
-      x.z ^= key;
-      x.w ^= key;
-      dv[i] = x;
-    }
+    if (kDepth > 4u) i = copy_xor_batches<(kDepth > 4u ? kDepth : 4u)>(dv, sv, nv, key, i, nthr);
+    if (kDepth > 1u) i = copy_xor_batches<(kDepth > 1u ? 4u : 1u)>(dv, sv, nv, key, i, nthr);
+    i = copy_xor_batches<1u>(dv, sv, nv, key, i, nthr);
     w0 = nv * 4u;
   }
   const uint32_t *sw = reinterpret_cast<const uint32_t *>(src);
@@ -688,8 +693,8 @@ __device__ __forceinline__ void worker_loop(const Env &e0) {
     const uint32_t work = c->work;
     if (work == kTerminate) break;
     if (work == kCopyWork) {
-      copy_xor<!P::kDense>(c->copy_dst, c->copy_src, c->copy_bytes, c->copy_key, threadIdx.x,
-                           W);
+      copy_xor<P::kDense ? 1u : kBatched ? 4u : 8u>(c->copy_dst, c->copy_src, c->copy_bytes,
+                                                   c->copy_key, threadIdx.x, W);
       named_arrive(kJoinBar, team_threads());
       continue;
     }

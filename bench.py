@@ -275,6 +275,25 @@ def _event_ms(torch, fn, reps, flush=None):
     return float(np.median(out))
 
 
+def _rotating_ms(torch, launch, n_sets, reps):
+    """Per-launch time of `reps` launches back to back between one pair of
+    events, launch i on input set i % n_sets (sets larger than L2 together,
+    so no launch finds its inputs in L2 from the set's last use)."""
+    s = torch.cuda.current_stream()
+    for i in range(n_sets):
+        launch(i)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    z = torch.cuda.Event(enable_timing=True)
+    torch.cuda._sleep(int(2.1e9 * (1e-3 + 50e-6 * reps)))  # the host queues ahead
+    a.record(s)
+    for i in range(reps):
+        launch(i)
+    z.record(s)
+    torch.cuda.synchronize()
+    return a.elapsed_time(z) / reps
+
+
 def smem_peak_gbs(sm_count: int, sm_mhz: float = 2070.0) -> float:
     """Shared-memory bandwidth bound: 128 bytes per clock per SM (32 banks
     of 4 bytes) at the maximum SM clock."""
@@ -293,11 +312,17 @@ def hetero_stack_bytes(regions) -> int:
     return total
 
 
+SWEEP_MAX_SETS = 80
+
+
 def measure_sweep(dsr, torch, device, flush, hbm_gbs, sizes=None):
     """The sweep: one fp32 frame per team, 512 teams x 128 threads, for each
     frame size placed in the shared-memory slab (when one CTA can hold it)
     and in the global overflow slab; HBM bytes per launch = images read +
-    outputs + statuses."""
+    outputs + statuses. Like the headline, a frame size whose buffers fit
+    SWEEP_MAX_SETS copies into more than twice the L2 is timed over rotating
+    copies launched back to back; smaller ones one launch at a time after
+    an L2 flush."""
     teams, threads = 512, 128
     rt = dsr.Runtime(device, slab_bytes=0, overflow_bytes_per_team=max(wl.SWEEP_SIZES),
                      max_teams=teams)
@@ -306,6 +331,12 @@ def measure_sweep(dsr, torch, device, flush, hbm_gbs, sizes=None):
         work = wl.sweep(S, teams=teams, threads=threads)
         region = work.regions[0]
         images, out, status = rt.device_buffers(work)
+        set_bytes = images.numel() + 4 * (out.numel() + status.numel())
+        n_sets = 1 + -(-ROTATE_BYTES // set_bytes)
+        sets = [(images, out, status)]
+        if n_sets <= SWEEP_MAX_SETS:
+            sets += [(images.clone(), torch.empty_like(out), torch.zeros_like(status))
+                     for _ in range(n_sets - 1)]
         for where in ("smem", "overflow"):
             if where == "smem":
                 if S + 384 > 232448:
@@ -314,9 +345,20 @@ def measure_sweep(dsr, torch, device, flush, hbm_gbs, sizes=None):
             else:
                 rt.configure(0, S, teams)
             occ = rt.occupancy(region)
-            ms = _event_ms(torch, lambda: dsr.dsr_launch_region(rt.ctx, region, images, out,
-                                                                status), 10, flush)
-            st = status.cpu().numpy().view(dsr.TEAM_STATUS_DTYPE)
+
+            def launch(i=0):
+                im, o, st_d = sets[i % len(sets)]
+                dsr.dsr_launch_region(rt.ctx, region, im, o, st_d)
+
+            if len(sets) > 1:
+                ms = _rotating_ms(torch, launch, len(sets), max(20, 2 * len(sets)))
+                timing = "%d rotating sets (%.0f MB), back to back" % (
+                    len(sets), len(sets) * set_bytes / 1e6)
+            else:
+                ms = _event_ms(torch, launch, 10, flush)
+                timing = "one launch per event pair after an L2 flush"
+            st = np.concatenate([x[2].cpu().numpy().view(dsr.TEAM_STATUS_DTYPE)
+                                 for x in sets])
             hbm = teams * S + teams * (threads - 32) * 4 + teams * 32
             gbs = hbm / (ms * 1e-3) / 1e9
             res.append(dict(frame_bytes=S, placement=where, us=ms * 1e3,
@@ -326,8 +368,8 @@ def measure_sweep(dsr, torch, device, flush, hbm_gbs, sizes=None):
                             smem_per_team=occ["smem_per_team"], ctas_per_sm=occ["ctas_per_sm"],
                             regs_per_thread=occ["regs_per_thread"],
                             spill_bytes_per_team=int(st["spill_bytes"].max()),
-                            bad_team_status=int((st["status"] != 0).sum())))
-        del images, out, status
+                            bad_team_status=int((st["status"] != 0).sum()), timing=timing))
+        del images, out, status, sets
     rt.close()
     return dict(workload="sweep_512x128", teams=teams, threads=threads, runs=res)
 

@@ -660,6 +660,29 @@ struct ProgWorkers {
   __device__ static void nested_phase(uint8_t *base, uint32_t l0, uint32_t l1, uint32_t L,
                                       uint32_t s1, uint32_t off_lane) {
     constexpr uint32_t kB = 4;
+    if ((L & 31u) == 0) {
+      // L a multiple of 32: the frames lie back to back (a frame's slot is
+      // exactly 4 L bytes) and each step of the lanes covers 32 consecutive
+      // words of one frame, so a counter gives each word's index in its
+      // frame, and no slot offset or walk is needed
+      uint32_t *p = reinterpret_cast<uint32_t *>(base) + lane_id();
+      const uint32_t rows = (l1 - l0) * (L >> 5);
+      uint32_t w = lane_id();  // index in its frame of this lane's word of row r
+      for (uint32_t r = 0; r < rows; r += kB) {
+        uint32_t v[kB], ww[kB];
+#pragma unroll
+        for (uint32_t u = 0; u < kB; ++u) {
+          ww[u] = w;
+          v[u] = r + u < rows ? p[32u * (r + u)] : 0u;
+          w += 32u;
+          if (w >= L) w -= L;
+        }
+#pragma unroll
+        for (uint32_t u = 0; u < kB; ++u)
+          if (r + u < rows) p[32u * (r + u)] = mix32(v[u] + s1 + ww[u]);
+      }
+      return;
+    }
     const uint32_t total = (l1 - l0) * L;
     Walk it(l0, L);
     for (uint32_t i = lane_id(); i < ((total + 32u * kB - 1u) & ~(32u * kB - 1u));

@@ -236,6 +236,8 @@ def _workers_slab(threads, S, frames_per_warp=32):
     (2, 1024, 36, 0),     # 31 worker warps, frames of 9 words
     (7, 96, 1028, 33),    # frames of 257 words, a warp with one worker
     (1, 128, 4, 1),       # one worker, one word
+    (3, 192, 384, 70),    # frames of 96 words (rows of 32), warps of 32, 32 and 6 workers
+    (2, 256, 128, 0),     # frames of one row of 32 words
 ])
 def test_workers_parity(rt, teams, threads, S, width):
     work = wl.workers(teams=teams, threads=threads, frame_bytes=S, width=width)
@@ -245,8 +247,9 @@ def test_workers_parity(rt, teams, threads, S, width):
     assert (gs["status"] == 0).all() and (gs["depth_final"] == 0).all()
 
 
-def test_workers_spill_to_overflow_shares(rt):
-    S, fp = 200, 208
+@pytest.mark.parametrize("S", [200, 256])  # frames of 50 words; of two rows of 32
+def test_workers_spill_to_overflow_shares(rt, S):
+    fp = (S + 15) // 16 * 16
     work = wl.workers(teams=6, threads=96, frame_bytes=S, width=40)
     # slab shares of 10 frames, overflow shares of 22; then all in overflow
     for slab, ovf in [(16 + 2 * 10 * fp, 2 * 22 * fp), (0, 16 + 2 * 32 * fp)]:

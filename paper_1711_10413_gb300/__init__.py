@@ -116,6 +116,7 @@ def _declare(L):
                                        _vp, _vp, _vp, _vp]),
         "dsr_enqueue_region_host": (_i32, [_vp, P(dsr_region_desc), _vp, _u64, _vp, _u64, _vp,
                                            _vp, _vp, _vp, _vp]),
+        "dsr_check_bounded_wait": (_i32, [_vp, _u64, _vp, _vp]),
         "dsr_batch_workspace_bytes": (_u64, [_u32, _u64]),
         "dsr_batch_count": (_i32, [_vp, _u32, _u64, _u64, _u64, P(_u64)]),
         "dsr_launch_batch": (_i32, [_vp, _vp, _u32, _u32, _u64, _vp, _u64, _vp, _u64, _vp, _u64,
@@ -169,7 +170,7 @@ def exported_symbols():
             "dsr_launch_regions", "dsr_launch_batch_static", "dsr_batch_static_capacity",
             "dsr_serve_workspace_bytes", "dsr_serve_start",
             "dsr_serve_submit", "dsr_serve_poll", "dsr_serve_stop", "dsr_serve_stats",
-            "dsr_serve_bench", "dsr_launch_bench"]
+            "dsr_serve_bench", "dsr_launch_bench", "dsr_check_bounded_wait"]
 
 
 # ---------------------------------------------------------------------------
@@ -323,6 +324,14 @@ def dsr_enqueue_region_host(ctx: int, region, images_host, image_bytes: int, out
                                          _ptr(out_host), out_bytes, _ptr(status_host),
                                          _ptr(images_dev), _ptr(out_dev), _ptr(status_dev),
                                          _stream(stream)), ctx)
+
+
+def dsr_check_bounded_wait(ctx: int, timeout_ns: int, result, stream=None) -> None:
+    """result: a device tensor of two int64 (or more bytes): receives
+    {status, elapsed ns} of a device wait that nothing completes."""
+    if result is None or _nbytes(result) < 16:
+        raise ValueError("result must hold two 64-bit words")
+    _check(lib().dsr_check_bounded_wait(ctx, timeout_ns, _ptr(result), _stream(stream)), ctx)
 
 
 def _tuning(t):

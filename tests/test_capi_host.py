@@ -156,3 +156,8 @@ def test_footprint_model_spill_matches_the_oracle(L):
                 model = dsr.dsr_footprint_model(r, sl, 32)["spill_bytes"]
                 rows = _oracle_rows(work, i, sl, 1 << 30)
                 assert (rows["spill_bytes"] == model).all(), (work.name, r, sl)
+
+
+def test_bounded_wait_check_rejects_missing_context(L):
+    """Checked on the host before anything launches."""
+    assert L.dsr_check_bounded_wait(None, 1000, None, None) == dsr.DSR_ERR_INVALID

@@ -4,9 +4,10 @@
  * stack (Sec. 5.2). The runtime adds one more rule of its own: every wait on
  * the device (fills completing on an mbarrier, the streamed fill's chunks,
  * the server's polling) gives up after the context's timeout and reports
- * DSR_ERR_TIMEOUT instead of spinning on. The check below exercises that
- * rule on a wait that nothing completes, without faulting, trapping or
- * hanging the GPU.
+ * DSR_ERR_TIMEOUT instead of spinning on. The checks below exercise that
+ * rule on a wait that nothing completes, and the stack's error statuses on
+ * pushes and pops misused on purpose, without faulting, trapping or hanging
+ * the GPU.
  */
 #ifndef DSR_DIAG_H
 #define DSR_DIAG_H
@@ -29,6 +30,32 @@ extern "C" {
  * ctx, null result, timeout too long), DSR_ERR_CUDA (launch failure). */
 int32_t dsr_check_bounded_wait(dsr_ctx *ctx, uint64_t timeout_ns, uint64_t *result_dev,
                                void *stream);
+
+/* The team stack's push and pop (Sec. 5.2: frames allocated on the shared
+ * stack, the global-memory fallback, release in LIFO order), misused on
+ * purpose by one master warp with a 96-byte slab and a 64-byte overflow
+ * slab (scratch_dev, caller-owned device memory of at least 64 bytes,
+ * 16-byte aligned). result_dev (device memory, n_result >= 25 uint64_t)
+ * receives, in order:
+ *   team 1: pushes of 48, 40 and 64 bytes -> [0] first in the slab, [1]
+ *     second in the slab, [2] third in the overflow slab, [3] slab bytes
+ *     reserved (96), [4] overflow bytes reserved (64); a pop of the second
+ *     frame, not the top -> [5] its status (DSR_ERR_LIFO), [6] depth (3),
+ *     [7] slab bytes, [8] overflow bytes (nothing popped); the three pops in
+ *     order -> [9..11] their statuses (DSR_OK), [12] depth (0), [13] slab
+ *     bytes (0), [14] overflow bytes (0), [15] the team's status (the first
+ *     error, DSR_ERR_LIFO), [16] peak bytes (160), [17] peak overflow bytes
+ *     (64);
+ *   team 2: pushes of 48, 48, 64 and 16 bytes -> [18] status
+ *     (DSR_ERR_OVERFLOW), [19] the fourth push gave no frame (1), [20] depth
+ *     (3); a pop of the top frame with a wrong size -> [21] DSR_ERR_LIFO;
+ *   team 3: DSR_MAX_FRAMES + 1 pushes of 16 bytes -> [22] frames pushed
+ *     (DSR_MAX_FRAMES), [23] status (DSR_ERR_OVERFLOW: the frame table is
+ *     full), [24] depth (DSR_MAX_FRAMES).
+ * Asynchronous on `stream`. Errors: DSR_ERR_INVALID (no ctx, short result or
+ * scratch), DSR_ERR_CUDA (launch failure). */
+int32_t dsr_check_stack(dsr_ctx *ctx, uint64_t *result_dev, uint32_t n_result,
+                        void *scratch_dev, uint64_t scratch_bytes, void *stream);
 
 #ifdef __cplusplus
 }

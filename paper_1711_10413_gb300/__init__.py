@@ -117,6 +117,7 @@ def _declare(L):
         "dsr_enqueue_region_host": (_i32, [_vp, P(dsr_region_desc), _vp, _u64, _vp, _u64, _vp,
                                            _vp, _vp, _vp, _vp]),
         "dsr_check_bounded_wait": (_i32, [_vp, _u64, _vp, _vp]),
+        "dsr_check_stack": (_i32, [_vp, _vp, _u32, _vp, _u64, _vp]),
         "dsr_batch_workspace_bytes": (_u64, [_u32, _u64]),
         "dsr_batch_count": (_i32, [_vp, _u32, _u64, _u64, _u64, P(_u64)]),
         "dsr_launch_batch": (_i32, [_vp, _vp, _u32, _u32, _u64, _vp, _u64, _vp, _u64, _vp, _u64,
@@ -170,7 +171,8 @@ def exported_symbols():
             "dsr_launch_regions", "dsr_launch_batch_static", "dsr_batch_static_capacity",
             "dsr_serve_workspace_bytes", "dsr_serve_start",
             "dsr_serve_submit", "dsr_serve_poll", "dsr_serve_stop", "dsr_serve_stats",
-            "dsr_serve_bench", "dsr_launch_bench", "dsr_check_bounded_wait"]
+            "dsr_serve_bench", "dsr_launch_bench", "dsr_check_bounded_wait",
+            "dsr_check_stack"]
 
 
 # ---------------------------------------------------------------------------
@@ -332,6 +334,13 @@ def dsr_check_bounded_wait(ctx: int, timeout_ns: int, result, stream=None) -> No
     if result is None or _nbytes(result) < 16:
         raise ValueError("result must hold two 64-bit words")
     _check(lib().dsr_check_bounded_wait(ctx, timeout_ns, _ptr(result), _stream(stream)), ctx)
+
+
+def dsr_check_stack(ctx: int, result, scratch, stream=None) -> None:
+    """result: a device tensor of at least 25 int64; scratch: at least 64
+    device bytes (the check's overflow slab)."""
+    _check(lib().dsr_check_stack(ctx, _ptr(result), _nbytes(result) // 8, _ptr(scratch),
+                                 _nbytes(scratch), _stream(stream)), ctx)
 
 
 def _tuning(t):

@@ -227,8 +227,6 @@ struct Stack {
   __device__ __forceinline__ uint32_t depth() const { return (bits >> 12) & 0xfu; }
 };
 
-// Team setup (master warp): the stack starts empty. `first` initialises the
-// fill mbarrier (once per CTA).
 // Programmatic dependent launch (an attribute of the plain form's launch):
 // the next grid in the stream may be dispatched once every CTA of this grid
 // has signalled, so its CTAs are placed and set up while this grid drains;
@@ -242,6 +240,8 @@ __device__ __forceinline__ void wait_prerequisites() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// Team setup (master warp): the stack starts empty. `first` initialises the
+// fill mbarrier (once per CTA).
 __device__ __forceinline__ void team_setup(Stack &s, uint32_t slab_bytes, uint8_t *ovf,
                                            uint64_t ovf_bytes, uint64_t timeout_ns, bool first) {
   Ctrl *c = ctrl();

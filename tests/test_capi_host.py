@@ -161,3 +161,7 @@ def test_footprint_model_spill_matches_the_oracle(L):
 def test_bounded_wait_check_rejects_missing_context(L):
     """Checked on the host before anything launches."""
     assert L.dsr_check_bounded_wait(None, 1000, None, None) == dsr.DSR_ERR_INVALID
+
+
+def test_stack_check_rejects_bad_arguments(L):
+    assert L.dsr_check_stack(None, None, 0, None, 0, None) == dsr.DSR_ERR_INVALID

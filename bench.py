@@ -4,13 +4,20 @@ one process per GPU, each running its own independent regions).
 Default workload: the wide plain-launch configuration -- 1024 teams x 256
 threads, 3 nested levels each pushing a 1088-byte frame (16 int32 scalars
 + int32[256]), 4M int32 output -- one region instance per step, launched
-through the C ABI. Metric: regions/s, with push+pop/s beside it.
+through the C ABI. Metric: regions/s, with push+pop/s beside it. The steps
+run back to back between one pair of CUDA events, each on the next of a
+rotating set of copies of the region's buffers that together exceed twice
+the L2; one launch timed alone after an L2 flush is reported beside it. The
+end-to-end figure runs the same steps from pinned host buffers, alternating
+over two streams (upload, kernel and download of every step inside the
+timed region).
 
 The same JSON line also carries the other configurations and launch forms
 (`--forms none` skips them):
   sweep    - 512 teams x 128 threads, one fp32 frame of 64 B .. 192 KiB per
              team, in the shared-memory slab and in the overflow slab: time,
-             HBM GB/s, occupancy and shared memory per team for each;
+             HBM GB/s, occupancy and shared memory per team for each (frames
+             of 8 KiB and up over rotating copies, back to back);
   scalars  - 1 team x 128 threads, 1000 sequential regions: one launch that
              runs them all against 1000 launches of one region each;
   batched  - 10,000 heterogeneous instances (log-uniform teams and frame
@@ -25,8 +32,9 @@ The same JSON line also carries the other configurations and launch forms
              on its warp, with the warp stacks in the slab and on the global
              stack.
 
-Prints ONE JSON line (rank 0). `--impl reference` times the CPU oracle on
-the same workload instead.
+Prints ONE JSON line (rank 0), with the CPU oracle timed beside it on a
+bounded sample (every host core, and one thread). `--impl reference` times
+the oracle alone on the same workload instead.
 """
 from __future__ import annotations
 

@@ -332,6 +332,7 @@ def measure_sweep(dsr, torch, device, flush, hbm_gbs, sizes=None):
     copies launched back to back; smaller ones one launch at a time after
     an L2 flush."""
     teams, threads = 512, 128
+    smem_peak = smem_peak_gbs(torch.cuda.get_device_properties(device).multi_processor_count)
     rt = dsr.Runtime(device, slab_bytes=0, overflow_bytes_per_team=max(wl.SWEEP_SIZES),
                      max_teams=teams)
     res = []
@@ -369,9 +370,14 @@ def measure_sweep(dsr, torch, device, flush, hbm_gbs, sizes=None):
                                  for x in sets])
             hbm = teams * S + teams * (threads - 32) * 4 + teams * 32
             gbs = hbm / (ms * 1e-3) / 1e9
+            # a frame in the slab: the fill writes S bytes of shared memory per
+            # team and the workers read them back
+            smem = 2 * teams * S if where == "smem" else 0
+            smem_gbs = smem / (ms * 1e-3) / 1e9
             res.append(dict(frame_bytes=S, placement=where, us=ms * 1e3,
                             regions_per_s=1.0 / (ms * 1e-3), hbm_bytes=hbm, hbm_gbs=gbs,
-                            hbm_frac=gbs / hbm_gbs,
+                            hbm_frac=gbs / hbm_gbs, smem_bytes=smem, smem_gbs=smem_gbs,
+                            smem_frac=smem_gbs / smem_peak,
                             overflow_bytes=2 * teams * S if where == "overflow" else 0,
                             smem_per_team=occ["smem_per_team"], ctas_per_sm=occ["ctas_per_sm"],
                             regs_per_thread=occ["regs_per_thread"],

@@ -4,6 +4,10 @@ Argument marshalling only: every call goes straight to the C ABI.
 """
 from __future__ import annotations
 
+import hashlib
+import json
+import os
+
 import numpy as np
 
 from . import (TEAM_STATUS_DTYPE, dsr_autotune, dsr_batch_count, dsr_batch_errors,
@@ -11,6 +15,35 @@ from . import (TEAM_STATUS_DTYPE, dsr_autotune, dsr_batch_count, dsr_batch_error
                dsr_launch_region, dsr_launch_regions, dsr_region_extent,
                dsr_region_occupancy, dsr_serve_start,
                dsr_serve_stop, dsr_serve_workspace_bytes, dsr_stack_init, pack_descs)
+
+
+def batch_class(descs: np.ndarray) -> str:
+    """Shape class of a batch, the autotuner cache's key: its programs, the
+    power of two below its instance count, and the rounded log2 of its mean
+    team count, mean threads per team and mean total frame bytes per team,
+    with its mean depth rounded. Batches drawn from one distribution get the
+    same class (a batch near a rounding edge may not: the tuner then runs
+    again); the images and outputs play no part."""
+    n = max(len(descs), 1)
+
+    def lg(v):
+        return int(round(float(np.log2(max(float(np.mean(v)), 1.0)))))
+
+    key = dict(program=sorted(set(int(p) for p in descs["program"])),
+               instances=int(np.floor(np.log2(n))),
+               teams=lg(descs["teams"]), threads=lg(descs["threads"]),
+               frames=lg(descs["frame_bytes"].sum(axis=1)),
+               depth=int(round(float(np.mean(descs["depth"])))))
+    return hashlib.sha256(json.dumps(key, sort_keys=True).encode()).hexdigest()[:16]
+
+
+def _load_cache(path: str) -> dict:
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d if isinstance(d, dict) else {}
+    except (OSError, ValueError):
+        return {}
 
 
 class Runtime:
@@ -111,6 +144,31 @@ class Runtime:
     def autotune(self, b, stream=None):
         return dsr_autotune(self.ctx, b["descs_dev"], len(b["descs"]), b["program"], b["total"],
                             b["images"], b["out"], b["status"], b["ws"], stream)
+
+    def device_key(self) -> str:
+        p = self.torch.cuda.get_device_properties(self.device)
+        return "%s/%d SMs" % (p.name, p.multi_processor_count)
+
+    def autotune_cached(self, b, path: str, stream=None, device_key=None):
+        """The autotuner's choice for this batch's device and shape class
+        (batch_class), from the JSON file at `path` when it holds one;
+        otherwise the autotuner runs (leaving the batch's outputs computed)
+        and its choice is added to the file. Returns (tuning, ms, hit); on a
+        hit nothing runs and ms is the time stored with the choice."""
+        key = "%s|%s" % (device_key or self.device_key(), batch_class(b["descs"]))
+        entry = _load_cache(path).get(key)
+        if entry:
+            t = entry["tuning"]
+            return (dict(threads=int(t["threads"]), slab_bytes=int(t["slab_bytes"]),
+                         ctas_per_sm=int(t["ctas_per_sm"])), float(entry["ms"]), True)
+        tuning, ms = self.autotune(b, stream)
+        cache = _load_cache(path)
+        cache[key] = dict(tuning=tuning, ms=ms)
+        tmp = "%s.%d.tmp" % (path, os.getpid())
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+        return tuning, ms, False
 
     def launch_regions(self, b, stream=None):
         dsr_launch_regions(self.ctx, b["descs"], b["images"], b["out"], b["status"], stream)

@@ -156,6 +156,24 @@ def test_autotune_returns_fitting_shape(rt):
     assert np.array_equal(g, r)
 
 
+def test_autotune_cache_hits_for_the_same_class(rt, tmp_path):
+    """The second batch of one distribution takes the tuned shape from the
+    cache file without tuning, and runs correctly with it."""
+    path = str(tmp_path / "tuning.json")
+    b1 = rt.batch_buffers(wl.hetero(n_instances=300, max_teams=32, seed=5))
+    best, ms, hit = rt.autotune_cached(b1, path)
+    assert not hit and ms > 0
+    work = wl.hetero(n_instances=300, max_teams=32, seed=6)
+    b2 = rt.batch_buffers(work)
+    best2, _, hit2 = rt.autotune_cached(b2, path)
+    assert hit2 and best2 == best
+    rt.launch_batch(b2, best2)
+    rt.torch.cuda.synchronize()
+    g, gs = rt.fetch(b2, work)
+    r, rs = oracle.run_workload(work, slab_bytes=best2["slab_bytes"], overflow_bytes=3 * 32768)
+    assert np.array_equal(g, r) and (gs["status"] == 0).all()
+
+
 def _sweep_batch(sizes, teams, threads=128, seed=7):
     """Several sweep instances in one batch: instance i has `teams` teams of
     one fp32 frame of sizes[i] bytes, its images and outputs packed."""

@@ -74,6 +74,40 @@ def test_serve_mix_equals_oracle(rt):
     assert stats["submitted"] == stats["completed"] == 400 and stats["errors"] == 0
 
 
+def test_serve_result_alone_equals_in_the_mix(rt):
+    """Every request in flight at once, then a sample of the same requests
+    served one at a time (each submitted only after the previous one has
+    completed) on fresh buffers: each sampled request's output rows and
+    team records are the same in both runs."""
+    import paper_1711_10413_gb300 as dsr
+    work = wl.hetero(n_instances=200, max_teams=24, seed=9)
+    b = rt.serve_start(work, threads=128, slab_bytes=8192, capacity=64)
+    try:
+        st = _wait_all(dsr, rt, _submit_all(dsr, rt, work.regions))
+    finally:
+        rt.serve_stop()
+    assert all(v == 0 for v in st.values())
+    mix_out = b["out"].cpu().numpy()
+    mix_st = b["status"].cpu().numpy().view(dsr.TEAM_STATUS_DTYPE)
+    sample = sorted(np.random.default_rng(3).choice(200, 12, replace=False).tolist())
+    b = rt.serve_start(work, threads=128, slab_bytes=8192, capacity=64)
+    try:
+        for i in sample:
+            st = _wait_all(dsr, rt, _submit_all(dsr, rt, [work.regions[i]]))
+            assert list(st.values()) == [0]
+    finally:
+        rt.serve_stop()
+    out = b["out"].cpu().numpy()
+    sts = b["status"].cpu().numpy().view(dsr.TEAM_STATUS_DTYPE)
+    for i in sample:
+        reg = work.regions[i]
+        o0, n = reg.out_offset // 4, reg.teams * reg.team_width
+        assert np.array_equal(out[o0:o0 + n], mix_out[o0:o0 + n]), i
+        s0 = reg.status_index
+        for f in ("status", "depth_final", "hwm_bytes", "spill_bytes", "chk"):
+            assert np.array_equal(sts[f][s0:s0 + reg.teams], mix_st[f][s0:s0 + reg.teams]), (i, f)
+
+
 def test_serve_open_loop_latencies(rt):
     import paper_1711_10413_gb300 as dsr
     work = wl.hetero(n_instances=3000, max_teams=64)

@@ -302,6 +302,20 @@ def _rotating_ms(torch, launch, n_sets, reps):
     return a.elapsed_time(z) / reps
 
 
+def smem_footprint(torch, rt, region, device):
+    """Shared memory the headline's resident teams hold on one SM, as a
+    share of the SM's shared memory, beside the paper's K40 figure for its
+    scalars program (context only: other hardware, another program)."""
+    occ = rt.occupancy(region)
+    props = torch.cuda.get_device_properties(device)
+    sm_bytes = getattr(props, "shared_memory_per_multiprocessor", 0) or 233472
+    held = occ["ctas_per_sm"] * occ["smem_per_team"]
+    return dict(per_team=occ["smem_per_team"], ctas_per_sm=occ["ctas_per_sm"],
+                bytes_per_sm=held, sm_bytes=sm_bytes, frac_of_sm=held / sm_bytes,
+                paper_context="K40, scalars program: at most 4332 bytes per SM, about 26 % "
+                              "of the 16 KB default shared memory (Sec. 6.3)")
+
+
 def smem_peak_gbs(sm_count: int, sm_mhz: float = 2070.0) -> float:
     """Shared-memory bandwidth bound: 128 bytes per clock per SM (32 banks
     of 4 bytes) at the maximum SM clock."""
@@ -785,6 +799,7 @@ def main():
             ms=ms_flushed, regions_per_s=regions_done * 1000.0 / ms_flushed,
             frac=algo_bytes / (ms_flushed * 1e-3) / 1e9 / peaks["hbm_gbs"],
             how="one launch between its own pair of events after a 256 MiB L2 flush"),
+        smem_footprint=smem_footprint(torch, rt, region, local),
         clocks=clk,
     )
     which = FORMS if args.forms == "all" else [f for f in args.forms.split(",")

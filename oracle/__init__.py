@@ -65,14 +65,15 @@ def _foreign(path: str) -> bool:
 
 
 def build(force: bool = False) -> str:
-    """Compile dsr_oracle.c into liboracle.so (plain gcc, -O2)."""
+    """Compile dsr_oracle.c into liboracle.so (plain gcc, -O2, no floating-point
+    contraction)."""
     with _lock:
         stale = (not os.path.exists(_LIB) or _foreign(_LIB)
                  or os.path.getmtime(_LIB) < os.path.getmtime(_SRC))
         if force or stale:
             tmp = _LIB + ".%d.tmp" % os.getpid()
-            subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC",
-                                   "-o", tmp, _SRC])
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-Wall",
+                                   "-shared", "-fPIC", "-o", tmp, _SRC])
             os.replace(tmp, _LIB)
     return _LIB
 
@@ -133,11 +134,11 @@ def run_workload(wl, slab_bytes: int = 1 << 62, overflow_bytes: int = 0,
                  regions: Optional[Sequence[int]] = None):
     """Run every (or the selected) region of a workload; returns (out, status).
 
-    The sweep program's output comes back as float64 pairs (sum, sum of
-    magnitudes) per output slot.
+    The sweep program's output comes back as float64 triples per output slot
+    (fp64 sum, fp64 sum of magnitudes, fp32 sum); `sweep_fields` splits them.
     """
     if wl.out_dtype == "float32":
-        out = np.zeros(wl.out_bytes // 4 * 2, dtype=np.float64)
+        out = np.zeros(wl.out_bytes // 4 * 3, dtype=np.float64)
     else:
         out = np.zeros(wl.out_bytes // 4, dtype=np.int32)
         if wl.out_init is not None:
@@ -149,6 +150,14 @@ def run_workload(wl, slab_bytes: int = 1 << 62, overflow_bytes: int = 0,
         if rc != OK:
             raise ValueError("oracle rejected region %d (rc=%d)" % (i, rc))
     return out, status
+
+
+def sweep_fields(out: np.ndarray):
+    """Split the sweep program's oracle output into its three per-slot
+    values: the fp64 sum, the fp64 sum of magnitudes (for the error bound)
+    and the fp32 sum in index order (float32, the program's own result)."""
+    t = out.reshape(-1, 3)
+    return t[:, 0], t[:, 1], t[:, 2].astype(np.float32)
 
 
 class Stack:

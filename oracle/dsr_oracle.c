@@ -31,8 +31,11 @@
  *
  * Integer arithmetic is modulo 2^32. mix32 is the 32-bit finaliser of
  * MurmurHash3 (Austin Appleby, public domain), written from its published
- * description. Floating point: the FP32 sweep program's reference sums are
- * kept in double (fp64).
+ * description. Floating point: the FP32 sweep program's sums are kept two
+ * ways: in double (fp64), with the sum of magnitudes for the error bound,
+ * and as the fp32 sum itself, taken in index order with every addition
+ * rounded to fp32 (the program's definition; this file is compiled with
+ * -ffp-contract=off, and the sum has no multiply to contract anyway).
  *
  * The region programs (shared locals, sequential code, bodies) are defined
  * in the comments of each team_* function below; W = threads - 32 is the
@@ -315,8 +318,10 @@ static void team_nested(const orc_region *d, uint32_t team, const uint8_t *img,
 /* ------------------------------------------------------------------------ */
 /* P3 "sweep": one frame float arr[L], L = S/4. Master: arr = image[team].   */
 /* Parallel: out[team*W' + tid] = arr[tid] + arr[tid+W'] + arr[tid+2W'] ... */
-/* (index order). The oracle keeps the sum, and the sum of magnitudes for   */
-/* the error bound, in double: out is double[T][W'][2].                     */
+/* (index order, each addition rounded to fp32). The oracle keeps three     */
+/* values per output slot: the sum and the sum of magnitudes (for the error */
+/* bound) in double, and the fp32 sum as defined, widened to double: out is */
+/* double[T][W'][3].                                                        */
 /* ------------------------------------------------------------------------ */
 static void team_sweep(const orc_region *d, uint32_t team, const uint8_t *img,
                        uint8_t *out, orc_stack *s) {
@@ -324,18 +329,21 @@ static void team_sweep(const orc_region *d, uint32_t team, const uint8_t *img,
   uint8_t *f = push(s, d->frame_bytes[0]);
   if (!f) return;
   memcpy(f, img + d->image_offset + (uint64_t)team * L * 4, (size_t)L * 4);
-  /* each 4-byte output slot of the product becomes 16 bytes here */
-  double *o = (double *)(out + 4 * d->out_offset);
+  /* each 4-byte output slot of the product becomes 24 bytes here */
+  double *o = (double *)(out + 6 * d->out_offset);
   for (uint32_t tid = 0; tid < w; tid++) {
     double sum = 0.0, mag = 0.0;
+    float sum32 = 0.0f;
     for (uint32_t i = tid; i < L; i += w) {
       float x;
       memcpy(&x, f + 4ull * i, 4);
       sum += (double)x;
       mag += x < 0 ? -(double)x : (double)x;
+      sum32 = sum32 + x;
     }
-    o[2 * ((uint64_t)team * w + tid)] = sum;
-    o[2 * ((uint64_t)team * w + tid) + 1] = mag;
+    o[3 * ((uint64_t)team * w + tid)] = sum;
+    o[3 * ((uint64_t)team * w + tid) + 1] = mag;
+    o[3 * ((uint64_t)team * w + tid) + 2] = (double)sum32;
   }
   pop(s, f);
 }
@@ -505,7 +513,8 @@ static int check_region(const orc_region *d) {
  * Run teams [team_begin, team_end) of one region instance.
  *   images: the image buffer (the descriptor's image_offset indexes it).
  *   out:    the output buffer (out_offset indexes it). For the sweep
- *           program it holds double[T][W'][2] (sum, sum of magnitudes).
+ *           program it holds double[T][W'][3] (fp64 sum, fp64 sum of
+ *           magnitudes, fp32 sum), at 6 * out_offset bytes.
  *   status: the team-status array; team t writes status[status_index + t].
  *   slab_bytes / overflow_bytes: stack capacities per team.
  * Returns ORC_OK, or ORC_ERR_INVALID for a malformed descriptor.

@@ -213,14 +213,12 @@ def test_batch_sweep_streams_across_tasks():
             T, W, L = reg.teams, reg.team_width, reg.frame_bytes[0] // 4
             o0 = reg.out_offset // 4
             got = g[o0:o0 + T * W].reshape(T, W)
-            ref = r[2 * o0: 2 * (o0 + T * W)][0::2].reshape(T, W)
-            # the same order on both sides: the fp32 sum taken left to right
-            x = work.images[reg.image_offset: reg.image_offset + T * L * 4].view(np.float32)
-            rows = (L + W - 1) // W
-            xp = np.zeros((T, rows * W), dtype=np.float32)
-            xp[:, :L] = x.reshape(T, L)
-            seq = np.add.accumulate(xp.reshape(T, rows, W), axis=1, dtype=np.float32)[:, -1, :]
-            assert np.array_equal(got, seq)
-            assert np.allclose(got, ref, rtol=1e-4, atol=1e-3)
+            s64, mag, s32 = oracle.sweep_fields(r[3 * o0: 3 * (o0 + T * W)])
+            # the oracle's fp32 index-order sum, bit for bit
+            assert np.array_equal(got.view(np.uint32), s32.reshape(T, W).view(np.uint32))
+            n = np.array([max(0, (L - t + W - 1) // W) for t in range(W)], dtype=np.float64)
+            gamma = (n - 1).clip(0) * 2.0 ** -24 / (1 - (n - 1).clip(0) * 2.0 ** -24)
+            tol = 1e-6 * np.abs(s64.reshape(T, W)) + gamma[None, :] * mag.reshape(T, W)
+            assert (np.abs(got.astype(np.float64) - s64.reshape(T, W)) <= tol).all()
     finally:
         rt.close()

@@ -4,7 +4,8 @@
   verification value (tests/golden/murmur3_x86_32.txt).
 * The paper's two evaluation programs (Sec. 6.1) against their closed forms.
 * The scalars body against hand-evaluated values (tests/golden).
-* The FP32 sweep against exactly rounded sums and closed-form counts.
+* The FP32 sweep against exactly rounded sums, closed-form counts, and
+  hand-derived worked examples of its fp32 index-order sum.
 * The nested / hetero programs against invariants that any correct
   implementation satisfies (stack depth back to 0, high-water marks, the
   structure that mix32 being a bijection exposes, placement independence).
@@ -162,28 +163,98 @@ def test_sweep_all_ones_counts(frame_bytes):
     work = wl.Workload("t", [region], images.view(np.uint8), 4 * teams * 96, teams,
                        out_dtype="float32")
     out, st = oracle.run_workload(work)
-    sums = out[0::2].reshape(teams, 96)
+    s64, _, s32 = oracle.sweep_fields(out)
+    sums, sums32 = s64.reshape(teams, 96), s32.reshape(teams, 96)
     for tid in range(96):
         # elements tid, tid + 96, ... below L
         count = 0 if tid >= L else (L - tid + 95) // 96
         assert (sums[:, tid] == count).all()
+        assert (sums32[:, tid] == np.float32(count)).all()
     assert (st["hwm_bytes"] == (frame_bytes + 15) // 16 * 16).all()
+
+
+def _gamma(n):
+    """gamma_n = n u / (1 - n u), u = 2^-24: the a-priori bound of recursive
+    fp32 summation of n + 1 terms is gamma_n times the sum of magnitudes."""
+    return n * U32 / (1 - n * U32)
+
+
+U32 = 2.0 ** -24
 
 
 @pytest.mark.parametrize("frame_bytes", [64, 1024, 32768])
 def test_sweep_matches_exact_sum(frame_bytes):
     w = wl.sweep(frame_bytes, teams=4)
     out, _ = oracle.run_workload(w)
-    sums = out[0::2].reshape(4, 96)
-    mags = out[1::2].reshape(4, 96)
+    s64, m64, s32 = oracle.sweep_fields(out)
+    sums, mags, sums32 = s64.reshape(4, 96), m64.reshape(4, 96), s32.reshape(4, 96)
     x = w.images.view(np.float32).reshape(4, frame_bytes // 4).astype(np.float64)
     for t in range(4):
         for tid in range(96):
             part = x[t, tid::96].tolist()
             exact = math.fsum(part)
-            bound = len(part) * 2.0 ** -53 * math.fsum(abs(v) for v in part)
+            mag = math.fsum(abs(v) for v in part)
+            bound = len(part) * 2.0 ** -53 * mag
             assert abs(sums[t, tid] - exact) <= bound
-            assert abs(mags[t, tid] - math.fsum(abs(v) for v in part)) <= bound
+            assert abs(mags[t, tid] - mag) <= bound
+            # the fp32 sum within the recursive-summation bound of the exact sum
+            assert abs(float(sums32[t, tid]) - exact) <= _gamma(max(len(part) - 1, 0)) * mag
+
+
+def _one_worker_sweep(values):
+    """One team of 64 threads (32 workers) whose worker 0 sums `values`
+    (elements 0, 32, 64, ...); the other slots hold zeros."""
+    L = 32 * len(values)
+    x = np.zeros(L, dtype=np.float32)
+    x[0::32] = np.asarray(values, dtype=np.float32)
+    region = wl.Region(wl.PROG_SWEEP, 1, 64, 1, [4 * L])
+    work = wl.Workload("t", [region], x.view(np.uint8), 4 * 32, 1, out_dtype="float32")
+    out, _ = oracle.run_workload(work)
+    s64, _, s32 = oracle.sweep_fields(out)
+    return float(s64[0]), s32[0]
+
+
+def test_sweep_fp32_order_and_rounding_worked_example():
+    """Worked example with hand-derived results. 1 + 2^-24 is a tie between 1
+    and 1 + 2^-23 and rounds to even (1), so in index order each small term
+    vanishes: [1, 2^-24, 2^-24, 2^-24] sums to exactly 1 in fp32. Taken the
+    other way round the small terms first add to 3 * 2^-24 exactly, and
+    1 + 3 * 2^-24 (1.5 ulp above 1) rounds to even, 1 + 2^-22. The fp64 sum
+    is exact, 1 + 3 * 2^-24. A sum in another order, in a wider type, or
+    with a fused step gives one of the other values."""
+    e = 2.0 ** -24
+    s64, s32 = _one_worker_sweep([1.0, e, e, e])
+    assert s32 == np.float32(1.0)
+    assert s64 == 1.0 + 3 * e
+    s64, s32 = _one_worker_sweep([e, e, e, 1.0])
+    assert s32 == np.float32(1.0 + 2.0 ** -22)
+    assert s64 == 1.0 + 3 * e
+
+
+def test_sweep_fp32_cancellation_worked_example():
+    """Catastrophic cancellation by hand: in fp32, 2^24 + 1 rounds to 2^24
+    (a tie, to even), so [2^24, 1, -2^24] sums to 0 while the exact (fp64)
+    sum is 1; [2^24, -2^24, 1] sums to 1 in both."""
+    s64, s32 = _one_worker_sweep([2.0 ** 24, 1.0, -(2.0 ** 24)])
+    assert s32 == np.float32(0.0) and s64 == 1.0
+    s64, s32 = _one_worker_sweep([2.0 ** 24, -(2.0 ** 24), 1.0])
+    assert s32 == np.float32(1.0) and s64 == 1.0
+
+
+def test_sweep_fp32_equals_numpy_left_to_right():
+    """The oracle's fp32 sums against numpy's fp32 running sum in index order
+    (np.add.accumulate over rows of W elements), an implementation of its
+    own, on a ragged frame (L not a multiple of the width)."""
+    w = wl.sweep(4 * 1001, teams=3, threads=160)
+    out, _ = oracle.run_workload(w)
+    _, _, s32 = oracle.sweep_fields(out)
+    W, L = 128, 1001
+    x = w.images.view(np.float32).reshape(3, L)
+    rows = (L + W - 1) // W
+    xp = np.zeros((3, rows * W), dtype=np.float32)
+    xp[:, :L] = x
+    seq = np.add.accumulate(xp.reshape(3, rows, W), axis=1, dtype=np.float32)[:, -1, :]
+    assert np.array_equal(s32.reshape(3, W), seq)
 
 
 # ---------------------------------------------------------------------------

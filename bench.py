@@ -64,15 +64,17 @@ ROTATE_BYTES = 264 << 20    # > twice the 129 MB L2: the headline's rotating inp
 # with 8 KiB slabs (the most resident CTAs) the highest capacity.
 SERVE_SHAPES = [dict(threads=256, slab_bytes=16384), dict(threads=128, slab_bytes=8192)]
 
-# DRAM traffic (read + write bytes per launch) of the plain nested kernel from
-# one ncu capture (profiles/nested_1024x256_d3_full.md), keyed by a hash of
-# the code of the sources that kernel is built from (comments and white
-# space left out); any change to that code makes it null.
-TRAFFIC_BY_SOURCE = {"9d723a9e3acd3e7d": 3393024}
-KERNEL_SOURCES = ["paper_1711_10413_gb300/csrc/dsr_runtime.cuh",
-                  "paper_1711_10413_gb300/csrc/dsr_programs.cuh",
-                  "paper_1711_10413_gb300/csrc/dsr_check.cuh",
-                  "paper_1711_10413_gb300/csrc/dsr_capi.cu", "include/dsr.h"]
+# DRAM traffic per launch of the plain nested kernel in the headline's steady
+# state (launches back to back over the rotating input sets, so each launch
+# also writes back the output lines an earlier launch left dirty in L2):
+# dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture
+# (profiles/nested_1024x256_d3_traffic.md), keyed by a hash of the code of
+# the sources that kernel is built from (comments and white space left
+# out); any change to that code makes it null.
+TRAFFIC_BY_SOURCE = {}
+KERNEL_SOURCES = ["include/dsr_runtime.cuh", "include/dsr_check.cuh", "include/dsr_kernels.cuh",
+                  "include/dsr.h", "paper_1711_10413_gb300/csrc/dsr_programs.cuh",
+                  "paper_1711_10413_gb300/csrc/dsr_capi.cu"]
 
 
 def _code_only(text: str) -> str:
@@ -83,13 +85,18 @@ def _code_only(text: str) -> str:
     return "".join(text.split())
 
 
-def _traffic():
+def source_key() -> str:
+    """Hash of the code of the headline kernel's sources."""
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, f)) as fh:
             h.update(_code_only(fh.read()).encode())
-    return TRAFFIC_BY_SOURCE.get(h.hexdigest()[:16])
+    return h.hexdigest()[:16]
+
+
+def _traffic():
+    return TRAFFIC_BY_SOURCE.get(source_key())
 
 
 def _peaks():
@@ -104,6 +111,22 @@ def _peaks():
 # ---------------------------------------------------------------------------
 # Workloads
 # ---------------------------------------------------------------------------
+def rotating_sets(work):
+    """(bytes of one copy of a region's buffers, copies whose total exceeds
+    twice the L2): the headline's inputs larger than L2."""
+    set_bytes = (work.images.nbytes + 4 * (max(work.out_bytes, 16) // 4) + 32 * work.n_status)
+    return set_bytes, 1 + -(-ROTATE_BYTES // set_bytes)
+
+
+def bench_config(cfg, work, world: int) -> dict:
+    """The `config` both arms print (the same dict for the same workload)."""
+    set_bytes, n_sets = rotating_sets(work)
+    return dict(cfg, parallelism="independent regions per GPU" if world > 1 else "1 GPU",
+                l2="inputs larger than L2: %d rotating sets of the region's buffers "
+                   "(%.1f MB each, %.0f MB in all), launched back to back"
+                   % (n_sets, set_bytes / 1e6, n_sets * set_bytes / 1e6))
+
+
 def make_workload(name: str, rank: int = 0):
     seed = wl.DEFAULT_SEED + 7919 * rank
     if name == "nested":
@@ -613,7 +636,8 @@ def main():
         line = dict(impl="reference", metric="regions/s", value=v, unit="regions/s",
                     n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
                     ms_per_step=1000.0 / v, higher_is_better=True, scaling="weak",
-                    vs_baseline=None, dtype="int32", data="synthetic", config=cfg,
+                    vs_baseline=None, dtype="int32", data="synthetic",
+                    config=bench_config(cfg, work, args.gpus),
                     e2e=dict(value=v, unit="regions/s", h2d_bytes_per_step=0,
                              d2h_bytes_per_step=0),
                     cpu_baseline=dict(value=v, unit="regions/s", cores=samples[-1]["cores"],
@@ -645,8 +669,8 @@ def main():
     # sets, more than twice the L2, pass through it, so no launch finds its
     # images or output lines in L2 from the last time, and the timed launches
     # run back to back with no flush between them.
-    set_bytes = images.numel() * images.element_size() + 4 * (out.numel() + status.numel())
-    n_sets = 1 + -(-ROTATE_BYTES // set_bytes)
+    set_bytes, n_sets = rotating_sets(work)
+    assert set_bytes == images.numel() * images.element_size() + 4 * (out.numel() + status.numel())
     sets = [(images, out, status)] + [
         (images.clone(), torch.empty_like(out), torch.zeros_like(status))
         for _ in range(n_sets - 1)]
@@ -655,7 +679,8 @@ def main():
         im, o, st = sets[i % n_sets]
         dsr.dsr_launch_region(rt.ctx, region, im, o, st, stream)
 
-    for i in range(max(args.warmup, n_sets)):
+    warmup_launches = max(args.warmup, n_sets)  # every set used once before timing
+    for i in range(warmup_launches):
         step(i)
     torch.cuda.synchronize()
 
@@ -778,10 +803,8 @@ def main():
         metric="regions/s", value=regions_per_s, unit="regions/s", n_gpus=world,
         steps=args.steps, warmup=args.warmup, ms_per_step=ms_step, higher_is_better=True,
         scaling="weak", vs_baseline=None, dtype="int32", data="synthetic",
-        config=dict(cfg, parallelism="independent regions per GPU" if world > 1 else "1 GPU",
-                    l2="inputs larger than L2: %d rotating sets of the region's buffers "
-                       "(%.1f MB each, %.0f MB in all), launched back to back"
-                       % (n_sets, set_bytes / 1e6, n_sets * set_bytes / 1e6)),
+        config=bench_config(cfg, work, world),
+        warmup_launches=warmup_launches,
         push_pop_per_s=regions_per_s * region.teams * region.depth,
         roofline=dict(bound="hbm", achieved=achieved, peak=peaks["hbm_gbs"], unit="GB/s",
                       frac=achieved / peaks["hbm_gbs"], traffic=_traffic(),

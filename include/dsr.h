@@ -99,7 +99,14 @@ enum {
    * the team's slab and overflow slab have left, evenly over the W/32
    * worker warps; a worker frame that fits neither share gives OVERFLOW.
    * chk[0] = sum of the team's outputs. Plain launch only. */
-  DSR_PROG_WORKERS = 7
+  DSR_PROG_WORKERS = 7,
+  /* First id of user-written programs: a program written against the device
+   * API of dsr_device.cuh and launched through its launch templates carries
+   * an id >= DSR_PROG_USER in its descriptors. The library checks such a
+   * descriptor's shape (teams, threads, depth, frame sizes, alignment) and
+   * the buffer extents the program states; the frames and bodies are the
+   * program's own. */
+  DSR_PROG_USER = 256
 };
 
 /* One region instance: a target region with `teams` teams (one CTA each in
@@ -163,6 +170,12 @@ int32_t dsr_destroy(dsr_ctx *ctx);
 /* Text of the ctx's last failure ("" if none). Owned by the ctx; valid until
  * the next call on it. Accepts NULL (returns the process-wide last error). */
 const char *dsr_last_error_string(const dsr_ctx *ctx);
+
+/* Record a failure on ctx (its dsr_last_error_string becomes msg) and
+ * return code. For code built on this library -- the launch templates of
+ * dsr_device.cuh -- to report its own failures the way the library does.
+ * ctx may be NULL (only the process-wide last error is set). */
+int32_t dsr_report_error(dsr_ctx *ctx, int32_t code, const char *msg);
 
 /* ---- stacks (Sec. 5.3 shared stack, Sec. 5.2 global fallback) ---------- */
 
@@ -351,13 +364,17 @@ int32_t dsr_launch_regions(dsr_ctx *ctx, const dsr_region_desc *descs_host, uint
  * in a file-scope device array of dsr_batch_static_capacity() bytes (8 MiB:
  * about one million teams) that every GPU loading this library keeps until
  * the process exits. A batch whose workspace would be larger is refused
- * with DSR_ERR_BUDGET. The first call on a device finds the array's device
- * address (cudaGetSymbolAddress, with that device made current for the
- * call) and sets the kernels' shared-memory limit; make that first call
- * before any stream capture. All calls share the one array and leave its
- * contents behind (each call re-initialises what it reads), so calls whose
- * launches overlap on the GPU -- on different streams without ordering, or
- * from different threads -- race and must not be issued. Overflow slabs
+ * with DSR_ERR_BUDGET. The ctx's device must be the calling thread's
+ * current device (else DSR_ERR_INVALID, nothing runs). The first call on a
+ * device finds the array's device address (cudaGetSymbolAddress) and keeps
+ * it for the process, and the first call on a ctx sets the kernels'
+ * shared-memory limit; make the first call before any stream capture, and
+ * do not use this entry point across a cudaDeviceReset. All calls share the
+ * one array and leave its contents behind (each call re-initialises what it
+ * reads), so calls whose launches overlap on the GPU -- on different
+ * streams without ordering, or from different threads -- race and must not
+ * be issued. Device-side rejections (including teams that total_teams left
+ * no task slot for) are read with dsr_batch_static_errors. Overflow slabs
  * still come from the ctx's pool when dsr_stack_init configured one. */
 int32_t dsr_launch_batch_static(dsr_ctx *ctx, const dsr_region_desc *descs_dev, uint32_t n,
                                 uint32_t program, uint64_t total_teams, const void *images_dev,
@@ -367,6 +384,85 @@ int32_t dsr_launch_batch_static(dsr_ctx *ctx, const dsr_region_desc *descs_dev, 
 
 /* Size in bytes of the fixed workspace dsr_launch_batch_static uses. */
 uint64_t dsr_batch_static_capacity(void);
+
+/* dsr_batch_errors for the last dsr_launch_batch_static on the ctx's device:
+ * reads the fixed workspace's header (tasks rejected on the device, among
+ * them teams that total_teams left no task slot for, and tasks counted by
+ * its scan). Synchronises `stream`; the batch must have been enqueued on it
+ * (or completed). Errors: DSR_ERR_INVALID (no static batch ran on this
+ * device yet), DSR_ERR_CUDA. */
+int32_t dsr_batch_static_errors(dsr_ctx *ctx, uint32_t *errors, uint64_t *tasks_counted,
+                                void *stream);
+
+/* ---- launches of user-written programs (dsr_device.cuh) ----------------- */
+
+/* What a plain launch of a user-written program needs from the ctx: the
+ * stack configuration of dsr_stack_init resolved for one region. Filled by
+ * dsr_user_plain_config; the launch template of dsr_device.cuh passes it to
+ * the plain kernel compiled in the user's translation unit. */
+typedef struct dsr_plain_config {
+  void *pool_dev;        /* overflow pool (team t's slab at + t * ovf_per_team) */
+  uint64_t ovf_per_team; /* overflow-slab bytes per team, 0 = none */
+  uint64_t timeout_ns;   /* bound of every device-side wait */
+  uint32_t slab_bytes;   /* shared-memory slab of this launch */
+  uint32_t ctrl_bytes;   /* control block in front of the slab */
+  int32_t device;        /* the ctx's device */
+  uint32_t max_smem;     /* dynamic shared memory a CTA may opt in to */
+} dsr_plain_config;
+
+/* Check a plain launch of a user-written program (d->program >=
+ * DSR_PROG_USER) and resolve its stack configuration: the descriptor's
+ * shape, image_need bytes of images from d->image_offset within image_bytes
+ * and out_need bytes of output from d->out_offset within out_bytes (the
+ * extents the program states), d->teams statuses from d->status_index within
+ * n_status, non-null outputs, the ctx's device current on the calling thread
+ * and d->teams within the overflow slabs of dsr_stack_init. The slab is the
+ * ctx's (with DSR_SLAB_AUTO: the sum of the descriptor's 16-byte-rounded
+ * frame sizes, capped). Launches nothing. Errors: DSR_ERR_INVALID,
+ * DSR_ERR_BUDGET. */
+int32_t dsr_user_plain_config(dsr_ctx *ctx, const dsr_region_desc *d, uint64_t image_need,
+                              uint64_t out_need, uint64_t image_bytes, uint64_t out_bytes,
+                              uint64_t n_status, const void *out_dev, const void *status_dev,
+                              dsr_plain_config *cfg);
+
+/* Arguments of the persistent batched kernel: filled by dsr_batch_prepare
+ * and passed by value to the kernel (device pointers as void*). */
+typedef struct dsr_batch_plan {
+  const void *descs;    /* n descriptors (device) */
+  const void *tasks;    /* (instance, team) task list in the workspace */
+  void *hdr;            /* workspace header: cursors, counts, errors */
+  const void *images;
+  void *out;
+  void *status;         /* dsr_team_status[n_status] */
+  void *pool;           /* overflow pool, one slab per CTA */
+  uint64_t capacity;    /* task slots (= total_teams) */
+  uint64_t image_bytes;
+  uint64_t out_bytes;
+  uint64_t n_status;
+  uint64_t ovf_per_cta;
+  uint64_t timeout_ns;
+  uint32_t n;           /* instances */
+  uint32_t slab_bytes;  /* shared-memory slab per CTA */
+  uint32_t grid;        /* CTAs of the persistent launch */
+  uint32_t threads;     /* threads per CTA */
+} dsr_batch_plan;
+
+/* First half of a batched launch of program `program` (a built-in id or a
+ * user-written one): checks the arguments as dsr_launch_batch does (with
+ * the CTA shape `threads` x `slab_bytes`, and `ctas_per_sm` resident CTAs
+ * per SM, which the caller computed for the kernel it will launch), then
+ * enqueues on `stream` the scan of the instances' team counts and the
+ * expansion of the (instance, team) task list into the workspace, and fills
+ * *plan with the persistent kernel's grid and arguments. The caller then
+ * launches the kernel on the same stream with dynamic shared memory
+ * plan->slab_bytes + DSR control block (the launch template of
+ * dsr_device.cuh does both). Errors: as dsr_launch_batch. */
+int32_t dsr_batch_prepare(dsr_ctx *ctx, const dsr_region_desc *descs_dev, uint32_t n,
+                          uint32_t program, uint64_t total_teams, const void *images_dev,
+                          uint64_t image_bytes, void *out_dev, uint64_t out_bytes,
+                          dsr_team_status *status_dev, uint64_t n_status, void *workspace_dev,
+                          uint64_t workspace_bytes, uint32_t threads, uint32_t slab_bytes,
+                          uint32_t ctas_per_sm, void *stream, dsr_batch_plan *plan);
 
 /* ---- served form: a device-resident request loop ------------------------ */
 

@@ -57,13 +57,14 @@ DSR_HD int shape_error(const dsr_region_desc &d) {
       return 0;
     case DSR_PROG_WORKERS:
       return (d.depth != 2 || d.frame_bytes[0] != 16 || d.threads < 64) ? 4 : 0;
-    default:
-      return 5;
+    default:  // a user-written program (dsr_device.cuh) states its own layout
+      return d.program >= DSR_PROG_USER ? 0 : 5;
   }
 }
 
 // Input-image bytes, output bytes and status entries of a well-formed
-// descriptor.
+// descriptor of a built-in program (a user-written program's images and
+// outputs are its own: both 0 here).
 DSR_HD void extent(const dsr_region_desc &d, uint64_t *ib, uint64_t *ob, uint64_t *ns) {
   const uint64_t T = d.teams, w = desc_width(d);
   uint64_t i = 0, o = 0;

@@ -1,0 +1,262 @@
+// dsr_kernels.cuh -- the kernels every region program runs in: the plain
+// per-region kernel (one CTA per team) and the persistent batched kernel
+// (a fixed grid pulling (instance, team) tasks). Both are templates over a
+// program P, so the library's built-in programs and programs a user writes
+// against dsr_device.cuh are launched by the same code.
+//
+// A program P provides:
+//   static constexpr uint32_t kProgram;  the id its descriptors carry
+//   static constexpr bool kDense;        teams fill the GPU: 32 registers
+//   __device__ static void master(const Env &, Stack &);    sequential code
+//   __device__ static void run(const Env &, uint32_t work, uint32_t first,
+//                              uint32_t W, uint32_t n, uint32_t arg);
+//                                        a worker's share of a region
+// and, when its buffer extents are not those of a built-in program
+// (user-written programs), kUser = true and
+//   __host__ __device__ static void extent(const dsr_region_desc &,
+//                                          uint64_t *image_bytes,
+//                                          uint64_t *out_bytes);
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+
+#include "dsr.h"
+#include "dsr_check.cuh"
+#include "dsr_runtime.cuh"
+
+namespace dsr {
+
+// ---------------------------------------------------------------------------
+// Program traits
+// ---------------------------------------------------------------------------
+template <class P, class = void>
+struct is_user : std::false_type {};
+template <class P>
+struct is_user<P, std::void_t<decltype(P::kUser)>> : std::bool_constant<P::kUser> {};
+
+template <class P, class = void>
+struct wide_regs : std::false_type {};
+template <class P>
+struct wide_regs<P, std::void_t<decltype(P::kWideRegs)>> : std::bool_constant<P::kWideRegs> {};
+
+// Images, outputs and statuses of a well-formed descriptor of program P.
+template <class P>
+DSR_HD void program_extent(const dsr_region_desc &d, uint64_t *ib, uint64_t *ob, uint64_t *ns) {
+  if constexpr (is_user<P>::value) {
+    P::extent(d, ib, ob);
+    *ns = d.teams;
+  } else {
+    extent(d, ib, ob, ns);
+  }
+}
+
+// The descriptor is well formed for P and fits the buffers it indexes.
+template <class P>
+DSR_HD bool program_fits(const dsr_region_desc &d, uint64_t image_bytes, uint64_t out_bytes,
+                         uint64_t n_status) {
+  if (d.program != P::kProgram || shape_error(d) != 0) return false;
+  uint64_t ib, ob, ns;
+  program_extent<P>(d, &ib, &ob, &ns);
+  if (ib && (d.image_offset > image_bytes || ib > image_bytes - d.image_offset)) return false;
+  if (d.out_offset > out_bytes || ob > out_bytes - d.out_offset) return false;
+  return static_cast<uint64_t>(d.status_index) + ns <= n_status;
+}
+
+// ---------------------------------------------------------------------------
+// Plain kernel: one CTA per team (Sec. 4: a target region compiles to one
+// kernel with a fixed number of teams and threads; team = threadblock).
+// MAXT/MINB bound the registers so that teams of MAXT threads can reach
+// MINB resident CTAs per SM.
+// ---------------------------------------------------------------------------
+template <class P, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB)
+    plain_kernel(const __grid_constant__ dsr_region_desc d, const uint8_t *__restrict__ images,
+                 uint8_t *__restrict__ out, dsr_team_status *__restrict__ st,
+                 uint8_t *__restrict__ pool, uint64_t ovf_per_team, uint32_t slab_bytes,
+                 uint64_t timeout_ns) {
+  Env e;
+  e.d = &d;
+  e.images = images;
+  e.out = out;
+  e.team = blockIdx.x;
+  if (threadIdx.x == 0) signal_dependents();
+  if (threadIdx.x < team_workers()) {
+    wait_prerequisites();
+    worker_loop<P>(e);
+    return;
+  }
+  Stack s;
+  team_setup(s, slab_bytes,
+             ovf_per_team ? pool + static_cast<uint64_t>(blockIdx.x) * ovf_per_team : nullptr,
+             ovf_per_team, timeout_ns, true);
+  wait_prerequisites();  // the set-up above touches shared memory only
+  P::master(e, s);
+  terminate_workers();
+  team_report(e, s, st);
+}
+
+using PlainFn = void (*)(dsr_region_desc, const uint8_t *, uint8_t *, dsr_team_status *,
+                         uint8_t *, uint64_t, uint32_t, uint64_t);
+
+// The plain kernel instance for a CTA of `threads` threads. Programs whose
+// launches fill the GPU with many teams (P::kDense) are held to 32
+// registers, so 2048 threads per SM can be resident; those whose teams are
+// few per SM anyway (kWideRegs) get up to 85; the others 64.
+template <class P>
+PlainFn pick_plain(uint32_t threads) {
+  // resident CTAs of 256 threads the register budget is sized for
+  constexpr int k = P::kDense ? 8 : wide_regs<P>::value ? 3 : 4;
+  if (threads <= 128) return plain_kernel<P, 128, 2 * k>;
+  if (threads <= 256) return plain_kernel<P, 256, k>;
+  constexpr int k512 = k / 2 > 1 ? k / 2 : 1, k1024 = k / 4 > 1 ? k / 4 : 1;
+  if (threads <= 512) return plain_kernel<P, 512, k512>;
+  return plain_kernel<P, 1024, k1024>;
+}
+
+// ---------------------------------------------------------------------------
+// Batched form: the workspace header and the persistent kernel
+// ---------------------------------------------------------------------------
+// The task list is dealt to kGroups parts round robin (part g holds
+// positions g, g + kGroups, ...), each with its own cursor on its own
+// 128-byte line, so the CTAs' grabs spread over kGroups addresses while
+// every part still runs in longest-first order; a CTA starts on part
+// (block mod kGroups) and moves on to the next part when its own is used up.
+constexpr uint32_t kGroups = 32;
+constexpr uint32_t kBuckets = 32;  // cost classes, log2 of a team's estimated cost
+
+struct WsHeader {
+  unsigned long long total;  // tasks counted by the scan
+  unsigned int errors;       // tasks rejected on the device
+  unsigned int pad[29];
+  unsigned long long bucket_fill[kBuckets];  // next free task slot of each cost class
+  struct {
+    unsigned long long next;  // tasks of this part handed out
+    unsigned long long pad[15];
+  } cursor[kGroups];
+};
+static_assert(sizeof(WsHeader) == 128 + 8 * kBuckets + 128 * kGroups, "workspace header");
+
+// The persistent kernel's master warp pulls tasks in chunks of kGrab
+// consecutive tasks (consecutive teams of one instance share its descriptor
+// and images, which then hit in cache).
+constexpr uint32_t kGrab = 2;
+
+struct Feeder {
+  uint32_t g;        // current part
+  uint32_t visited;  // parts found used up
+
+  // Next chunk of tasks of the current part: positions [*start, *end) of
+  // the part (task index = g + position * kGroups); *start == *end when no
+  // task is left anywhere.
+  __device__ __forceinline__ void next(WsHeader *hdr, uint32_t total, uint32_t *start,
+                                       uint32_t *end) {
+    while (visited < kGroups) {
+      const uint32_t count = g < total ? (total - g + kGroups - 1) / kGroups : 0u;
+      unsigned long long t = 0;
+      if (lane_id() == 0)
+        t = atomicAdd(&hdr->cursor[g].next, static_cast<unsigned long long>(kGrab));
+      t = __shfl_sync(0xffffffffu, t, 0);
+      if (t < count) {
+        *start = static_cast<uint32_t>(t);
+        *end = min(*start + kGrab, count);
+        return;
+      }
+      g = (g + 1) % kGroups;
+      ++visited;
+    }
+    *start = *end = 0;
+  }
+  __device__ __forceinline__ uint32_t task_index(uint32_t pos) const { return g + pos * kGroups; }
+};
+
+// The persistent kernel. Each task runs as one team of its instance: the
+// descriptor is copied into the control block and checked once per
+// instance (a bad one gives its teams INVALID). The next chunk's grab and
+// the next task's entry are issued before the current task runs, so their
+// latency overlaps it.
+template <class P, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) batch_kernel(const __grid_constant__ dsr_batch_plan a) {
+  Env e;
+  e.d = nullptr;
+  e.images = static_cast<const uint8_t *>(a.images);
+  e.out = static_cast<uint8_t *>(a.out);
+  e.team = 0;
+  if (threadIdx.x < team_workers()) {
+    worker_loop<P, true>(e);
+    return;
+  }
+  Ctrl *c = ctrl();
+  Stack s;
+  WsHeader *hdr = static_cast<WsHeader *>(a.hdr);
+  const uint2 *tasks = static_cast<const uint2 *>(a.tasks);
+  const dsr_region_desc *descs = static_cast<const dsr_region_desc *>(a.descs);
+  dsr_team_status *status = static_cast<dsr_team_status *>(a.status);
+  uint8_t *ovf = a.ovf_per_cta ? static_cast<uint8_t *>(a.pool) +
+                                     static_cast<uint64_t>(blockIdx.x) * a.ovf_per_cta
+                               : nullptr;
+  const uint32_t total = static_cast<uint32_t>(min(static_cast<uint64_t>(hdr->total), a.capacity));
+  const uint32_t lane = lane_id();
+  Feeder feed{blockIdx.x % kGroups, 0};
+  uint32_t cur, end;
+  feed.next(hdr, total, &cur, &end);
+  bool have = cur < end;
+  uint2 task = have ? tasks[feed.task_index(cur)] : make_uint2(0, 0);
+  uint32_t cached = 0xffffffffu;  // instance whose descriptor is in the control block
+  bool cached_ok = false;
+  bool first = true;
+  while (have) {
+    // the next task: its chunk grab (at a chunk boundary) and its entry
+    uint32_t nxt = cur + 1, nend = end;
+    if (nxt >= end) feed.next(hdr, total, &nxt, &nend);
+    const bool nhave = nxt < nend;
+    const uint2 ntask = nhave ? tasks[feed.task_index(nxt)] : make_uint2(0, 0);
+
+    if (task.x != cached) {
+      __syncwarp();
+      if (lane < 4)
+        reinterpret_cast<uint4 *>(&c->desc)[lane] =
+            reinterpret_cast<const uint4 *>(descs + task.x)[lane];
+      __syncwarp();
+      cached = task.x;
+      cached_ok = program_fits<P>(c->desc, a.image_bytes, a.out_bytes, a.n_status);
+    }
+    if (lane == 0) c->team = task.y;
+    e.d = &c->desc;
+    e.team = task.y;
+    team_setup(s, a.slab_bytes, ovf, a.ovf_per_cta, a.timeout_ns, first);
+    first = false;
+    if (!cached_ok || task.y >= c->desc.teams) {
+      if (lane == 0) {
+        atomicAdd(&hdr->errors, 1u);
+        const uint64_t si = static_cast<uint64_t>(c->desc.status_index) + task.y;
+        if (si < a.n_status) {
+          dsr_team_status r = {};
+          r.status = DSR_ERR_INVALID;
+          status[si] = r;
+        }
+      }
+    } else {
+      P::master(e, s);
+      team_report(e, s, status);
+    }
+    cur = nxt;
+    end = nend;
+    task = ntask;
+    have = nhave;
+  }
+  terminate_workers();
+}
+
+using BatchFn = void (*)(dsr_batch_plan);
+
+// Three register budgets: small CTAs held to 32 registers so that many of
+// them (many tasks in flight) fit an SM; the others up to 64.
+template <class P>
+BatchFn pick_batch(uint32_t threads) {
+  if (threads <= 128) return batch_kernel<P, 128, 16>;
+  if (threads <= 256) return batch_kernel<P, 256, 4>;
+  return batch_kernel<P, 1024, 1>;
+}
+
+}  // namespace dsr

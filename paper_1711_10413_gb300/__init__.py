@@ -33,6 +33,7 @@ DSR_PROG_NESTED = 4
 DSR_PROG_SWEEP = 5
 DSR_PROG_HETERO = 6
 DSR_PROG_WORKERS = 7
+DSR_PROG_USER = 256
 
 
 class dsr_region_desc(ctypes.Structure):
@@ -62,6 +63,24 @@ class dsr_serve_cfg(ctypes.Structure):
                 ("image_bytes", ctypes.c_uint64), ("out_dev", ctypes.c_void_p),
                 ("out_bytes", ctypes.c_uint64), ("status_dev", ctypes.c_void_p),
                 ("n_status", ctypes.c_uint64)]
+
+
+class dsr_plain_config(ctypes.Structure):
+    _fields_ = [("pool_dev", ctypes.c_void_p), ("ovf_per_team", ctypes.c_uint64),
+                ("timeout_ns", ctypes.c_uint64), ("slab_bytes", ctypes.c_uint32),
+                ("ctrl_bytes", ctypes.c_uint32), ("device", ctypes.c_int32),
+                ("max_smem", ctypes.c_uint32)]
+
+
+class dsr_batch_plan(ctypes.Structure):
+    _fields_ = [("descs", ctypes.c_void_p), ("tasks", ctypes.c_void_p), ("hdr", ctypes.c_void_p),
+                ("images", ctypes.c_void_p), ("out", ctypes.c_void_p), ("status", ctypes.c_void_p),
+                ("pool", ctypes.c_void_p), ("capacity", ctypes.c_uint64),
+                ("image_bytes", ctypes.c_uint64), ("out_bytes", ctypes.c_uint64),
+                ("n_status", ctypes.c_uint64), ("ovf_per_cta", ctypes.c_uint64),
+                ("timeout_ns", ctypes.c_uint64), ("n", ctypes.c_uint32),
+                ("slab_bytes", ctypes.c_uint32), ("grid", ctypes.c_uint32),
+                ("threads", ctypes.c_uint32)]
 
 
 class dsr_footprint(ctypes.Structure):
@@ -129,6 +148,13 @@ def _declare(L):
         "dsr_launch_batch_static": (_i32, [_vp, _vp, _u32, _u32, _u64, _vp, _u64, _vp, _u64,
                                            _vp, _u64, P(dsr_batch_tuning), _vp]),
         "dsr_batch_static_capacity": (_u64, []),
+        "dsr_batch_static_errors": (_i32, [_vp, P(_u32), P(_u64), _vp]),
+        "dsr_report_error": (_i32, [_vp, _i32, ctypes.c_char_p]),
+        "dsr_user_plain_config": (_i32, [_vp, P(dsr_region_desc), _u64, _u64, _u64, _u64, _u64,
+                                         _vp, _vp, P(dsr_plain_config)]),
+        "dsr_batch_prepare": (_i32, [_vp, _vp, _u32, _u32, _u64, _vp, _u64, _vp, _u64, _vp,
+                                     _u64, _vp, _u64, _u32, _u32, _u32, _vp,
+                                     P(dsr_batch_plan)]),
         "dsr_serve_workspace_bytes": (_u64, [_u32]),
         "dsr_serve_start": (_i32, [_vp, P(dsr_serve_cfg), _vp, _u64]),
         "dsr_serve_submit": (_i32, [_vp, P(dsr_region_desc), P(_u64)]),
@@ -169,6 +195,8 @@ def exported_symbols():
             "dsr_batch_workspace_bytes",
             "dsr_batch_count", "dsr_launch_batch", "dsr_batch_errors", "dsr_autotune",
             "dsr_launch_regions", "dsr_launch_batch_static", "dsr_batch_static_capacity",
+            "dsr_batch_static_errors", "dsr_report_error", "dsr_user_plain_config",
+            "dsr_batch_prepare",
             "dsr_serve_workspace_bytes", "dsr_serve_start",
             "dsr_serve_submit", "dsr_serve_poll", "dsr_serve_stop", "dsr_serve_stats",
             "dsr_serve_bench", "dsr_launch_bench", "dsr_check_bounded_wait",
@@ -389,6 +417,30 @@ def dsr_launch_batch_static(ctx: int, descs_dev, n: int, program: int, total_tea
 
 def dsr_batch_static_capacity() -> int:
     return int(lib().dsr_batch_static_capacity())
+
+
+def dsr_batch_static_errors(ctx: int, stream=None):
+    """(tasks rejected on the device, tasks counted) of the last
+    dsr_launch_batch_static on the ctx's device (synchronises `stream`)."""
+    e, t = _u32(), _u64()
+    _check(lib().dsr_batch_static_errors(ctx, ctypes.byref(e), ctypes.byref(t),
+                                         _stream(stream)), ctx)
+    return int(e.value), int(t.value)
+
+
+def dsr_report_error(ctx: int, code: int, msg: str) -> int:
+    return int(lib().dsr_report_error(ctx, code, msg.encode()))
+
+
+def dsr_user_plain_config(ctx: int, region, image_need: int, out_need: int, image_bytes: int,
+                          out_bytes: int, n_status: int, out, status) -> dict:
+    """The checks and stack configuration of a plain launch of a user-written
+    program (what dsr_launch_user_region passes to its kernel)."""
+    c = dsr_plain_config()
+    _check(lib().dsr_user_plain_config(ctx, ctypes.byref(pack_desc(region)), image_need,
+                                       out_need, image_bytes, out_bytes, n_status, _ptr(out),
+                                       _ptr(status), ctypes.byref(c)), ctx)
+    return {f: getattr(c, f) for f, _ in dsr_plain_config._fields_}
 
 
 def dsr_batch_errors(ctx: int, workspace, stream=None):

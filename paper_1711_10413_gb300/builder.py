@@ -33,7 +33,8 @@ def _sources():
 
 def _deps():
     return (_sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
-            + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)])
+            + glob.glob(os.path.join(INCLUDE, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.cuh"))
+            + [os.path.abspath(__file__)])
 
 
 def _elf_machine(path: str) -> int:
@@ -88,6 +89,44 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
         os.replace(tmp, LIB)
         return LIB
+
+
+def build_user(sources, out: str, force: bool = False, ptxas_info: bool = False) -> str:
+    """Compile region programs written against include/dsr_device.cuh (the
+    .cu files `sources`) into the shared library `out`, linked with
+    libdsr.so (built first if needed); returns `out`. A program's kernels
+    are instantiated in its own library, from the same templates as the
+    built-in programs'."""
+    lib = build()
+    sources = [os.path.abspath(x) for x in sources]
+    with _lock:
+        deps = sources + _deps() + [lib]
+        fresh = (os.path.exists(out) and _elf_machine(out) == _host_machine()
+                 and all(os.path.getmtime(p) <= os.path.getmtime(out) for p in deps))
+        if fresh and not (force or ptxas_info):
+            return out
+        cc = nvcc()
+        extra = ["-Xptxas", "-v"] if ptxas_info else []
+        objs = []
+        os.makedirs(BUILD, exist_ok=True)
+        for src in sources:
+            obj = os.path.join(BUILD, "user_" + os.path.basename(src)[:-3] + ".o")
+            r = subprocess.run([cc, "-c", src, "-o", obj] + compile_flags(extra),
+                               capture_output=True, text=True)
+            if r.returncode != 0:
+                raise RuntimeError("nvcc failed on %s:\n%s%s" % (src, r.stdout, r.stderr))
+            if ptxas_info:
+                sys.stderr.write(r.stderr)
+            objs.append(obj)
+        tmp = out + ".%d.tmp" % os.getpid()
+        cmd = ([cc, "-shared", "-o", tmp] + objs + ARCH
+               + ["-cudart", "shared", "-L", PKG, "-ldsr", "-Xlinker", "-rpath=" + PKG,
+                  "-Xlinker", "-rpath=/usr/local/cuda/lib64"])
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
+        os.replace(tmp, out)
+        return out
 
 
 if __name__ == "__main__":

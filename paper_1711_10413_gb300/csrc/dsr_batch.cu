@@ -8,7 +8,10 @@
 // workers runs its threads round robin on them). Three kernels make a batch:
 // a scan of the instances' team counts, the expansion of the task list, and
 // the persistent kernel; with use_graph they are captured once per
-// argument set into a CUDA graph that later calls replay.
+// argument set into a CUDA graph that later calls replay. The persistent
+// kernel itself (batch_kernel in dsr_kernels.cuh) is a template over the
+// program, shared with programs written against dsr_device.cuh; this file
+// launches the built-in programs' instances and prepares every batch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,32 +22,12 @@
 #include "dsr.h"
 #include "dsr_check.cuh"
 #include "dsr_ctx.h"
+#include "dsr_kernels.cuh"
 #include "dsr_programs.cuh"
 
 using namespace dsr;
 
 namespace {
-
-// The task list is dealt to kGroups parts round robin (part g holds
-// positions g, g + kGroups, ...), each with its own cursor on its own
-// 128-byte line, so the CTAs' grabs spread over kGroups addresses while
-// every part still runs in longest-first order; a CTA starts on part
-// (block mod kGroups) and moves on to the next part when its own is used up.
-constexpr uint32_t kGroups = 32;
-
-constexpr uint32_t kBuckets = 32;  // cost classes, log2 of a team's estimated cost
-
-struct WsHeader {
-  unsigned long long total;  // tasks counted by the scan
-  unsigned int errors;       // tasks rejected on the device
-  unsigned int pad[29];
-  unsigned long long bucket_fill[kBuckets];  // next free task slot of each cost class
-  struct {
-    unsigned long long next;  // tasks of this part handed out
-    unsigned long long pad[15];
-  } cursor[kGroups];
-};
-static_assert(sizeof(WsHeader) == 128 + 8 * kBuckets + 128 * kGroups, "workspace header");
 
 constexpr uint64_t kWsHeader = sizeof(WsHeader);
 
@@ -52,24 +35,6 @@ uint64_t pad256(uint64_t n) { return (n + 255u) & ~static_cast<uint64_t>(255u); 
 
 uint64_t ws_tasks_off(uint32_t) { return pad256(kWsHeader); }
 uint64_t ws_bytes(uint32_t n, uint64_t tasks) { return ws_tasks_off(n) + pad256(8ull * tasks); }
-
-struct BatchArgs {
-  const dsr_region_desc *descs;
-  const uint2 *tasks;  // (instance, team)
-  WsHeader *hdr;
-  const uint8_t *images;
-  uint8_t *out;
-  dsr_team_status *status;
-  uint8_t *pool;
-  uint64_t capacity;  // task slots in the workspace
-  uint64_t image_bytes;
-  uint64_t out_bytes;
-  uint64_t n_status;
-  uint64_t ovf_per_cta;
-  uint64_t timeout_ns;
-  uint32_t n;
-  uint32_t slab_bytes;
-};
 
 // A team's estimated cost, in word-operations: its frames' words (filled,
 // updated and hashed once or twice each), its region width (one output per
@@ -110,135 +75,34 @@ __global__ void __launch_bounds__(1024) batch_scan(const dsr_region_desc *__rest
 // Task list: each instance claims a contiguous run of slots in its cost
 // class and writes its teams there (one warp per instance). The order of
 // instances inside a class depends on timing; which teams run is the same.
+// A team with no slot (the caller's total_teams fell short of the
+// instances' sum) never runs: its status says INVALID, where addressable,
+// and it counts as a device-side error.
 __global__ void __launch_bounds__(256) batch_expand(const dsr_region_desc *__restrict__ descs,
                                                     uint32_t n, WsHeader *hdr, uint2 *tasks,
-                                                    uint64_t capacity) {
+                                                    uint64_t capacity, dsr_team_status *status,
+                                                    uint64_t n_status) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warps = gridDim.x * (blockDim.x / 32u);
   for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) / 32u; i < n; i += warps) {
     const uint32_t T = descs[i].teams;
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&hdr->bucket_fill[cost_class(descs[i])], static_cast<unsigned long long>(T));
+    if (lane == 0)
+      base = atomicAdd(&hdr->bucket_fill[cost_class(descs[i])], static_cast<unsigned long long>(T));
     base = __shfl_sync(0xffffffffu, base, 0);
-    for (uint32_t t = lane; t < T && base + t < capacity; t += 32u)
-      tasks[base + t] = make_uint2(i, t);
-  }
-}
-
-// The persistent kernel. Its master warp pulls tasks in chunks of kGrab
-// consecutive tasks (consecutive teams of one instance share its descriptor
-// and images, which then hit in cache) and runs each as one team of its
-// instance: the descriptor is copied into the control block and checked
-// once per instance. The next chunk's grab and the next task's entry are
-// issued before the current task runs, so their latency overlaps it.
-constexpr uint32_t kGrab = 2;
-
-struct Feeder {
-  uint32_t g;        // current part
-  uint32_t visited;  // parts found used up
-
-  // Next chunk of tasks of the current part: positions [*start, *end) of
-  // the part (task index = g + position * kGroups); *start == *end when no
-  // task is left anywhere.
-  __device__ __forceinline__ void next(const BatchArgs &a, uint32_t total, uint32_t *start,
-                                       uint32_t *end) {
-    while (visited < kGroups) {
-      const uint32_t count = g < total ? (total - g + kGroups - 1) / kGroups : 0u;
-      unsigned long long t = 0;
-      if (lane_id() == 0) t = atomicAdd(&a.hdr->cursor[g].next, static_cast<unsigned long long>(kGrab));
-      t = __shfl_sync(0xffffffffu, t, 0);
-      if (t < count) {
-        *start = static_cast<uint32_t>(t);
-        *end = min(*start + kGrab, count);
-        return;
-      }
-      g = (g + 1) % kGroups;
-      ++visited;
+    const uint64_t room = base < capacity ? capacity - static_cast<uint64_t>(base) : 0u;
+    const uint64_t placed = T < room ? static_cast<uint64_t>(T) : room;
+    for (uint32_t t = lane; t < placed; t += 32u) tasks[base + t] = make_uint2(i, t);
+    if (placed < T) {
+      if (lane == 0) atomicAdd(&hdr->errors, static_cast<unsigned int>(T - placed));
+      const uint64_t si = descs[i].status_index;
+      const uint64_t addressable = si < n_status ? n_status - si : 0u;
+      const uint64_t stop = T < addressable ? static_cast<uint64_t>(T) : addressable;
+      dsr_team_status r = {};
+      r.status = DSR_ERR_INVALID;
+      for (uint64_t t = placed + lane; t < stop; t += 32u) status[si + t] = r;
     }
-    *start = *end = 0;
   }
-  __device__ __forceinline__ uint32_t task_index(uint32_t pos) const { return g + pos * kGroups; }
-};
-
-template <class P, int MAXT, int MINB>
-__global__ void __launch_bounds__(MAXT, MINB) batch_kernel(const __grid_constant__ BatchArgs a) {
-  Env e;
-  e.d = nullptr;
-  e.images = a.images;
-  e.out = a.out;
-  e.team = 0;
-  if (threadIdx.x < team_workers()) {
-    worker_loop<P, true>(e);
-    return;
-  }
-  Ctrl *c = ctrl();
-  Stack s;
-  uint8_t *ovf = a.ovf_per_cta ? a.pool + static_cast<uint64_t>(blockIdx.x) * a.ovf_per_cta : nullptr;
-  const uint32_t total =
-      static_cast<uint32_t>(min(static_cast<uint64_t>(a.hdr->total), a.capacity));
-  const uint32_t lane = lane_id();
-  Feeder feed{blockIdx.x % kGroups, 0};
-  uint32_t cur, end;
-  feed.next(a, total, &cur, &end);
-  bool have = cur < end;
-  uint2 task = have ? a.tasks[feed.task_index(cur)] : make_uint2(0, 0);
-  uint32_t cached = 0xffffffffu;  // instance whose descriptor is in the control block
-  bool cached_ok = false;
-  bool first = true;
-  while (have) {
-    // the next task: its chunk grab (at a chunk boundary) and its entry
-    uint32_t nxt = cur + 1, nend = end;
-    if (nxt >= end) feed.next(a, total, &nxt, &nend);
-    const bool nhave = nxt < nend;
-    const uint2 ntask = nhave ? a.tasks[feed.task_index(nxt)] : make_uint2(0, 0);
-
-    if (task.x != cached) {
-      __syncwarp();
-      if (lane < 4)
-        reinterpret_cast<uint4 *>(&c->desc)[lane] =
-            reinterpret_cast<const uint4 *>(a.descs + task.x)[lane];
-      __syncwarp();
-      const dsr_region_desc &d = c->desc;
-      cached = task.x;
-      cached_ok = d.program == P::kProgram && shape_error(d) == 0 &&
-                  fits(d, a.image_bytes, a.out_bytes, a.n_status);
-    }
-    if (lane == 0) c->team = task.y;
-    e.d = &c->desc;
-    e.team = task.y;
-    team_setup(s, a.slab_bytes, ovf, a.ovf_per_cta, a.timeout_ns, first);
-    first = false;
-    if (!cached_ok || task.y >= c->desc.teams) {
-      if (lane == 0) {
-        atomicAdd(&a.hdr->errors, 1u);
-        const uint64_t si = static_cast<uint64_t>(c->desc.status_index) + task.y;
-        if (si < a.n_status) {
-          dsr_team_status r = {};
-          r.status = DSR_ERR_INVALID;
-          a.status[si] = r;
-        }
-      }
-    } else {
-      P::master(e, s);
-      team_report(e, s, a.status);
-    }
-    cur = nxt;
-    end = nend;
-    task = ntask;
-    have = nhave;
-  }
-  terminate_workers();
-}
-
-using BatchFn = void (*)(BatchArgs);
-
-// Three register budgets: small CTAs held to 32 registers so that many of
-// them (many tasks in flight) fit an SM; the others up to 64.
-template <class P>
-BatchFn pick_batch(uint32_t threads) {
-  if (threads <= 128) return batch_kernel<P, 128, 16>;
-  if (threads <= 256) return batch_kernel<P, 256, 4>;
-  return batch_kernel<P, 1024, 1>;
 }
 
 BatchFn batch_kernel_for(uint32_t program, uint32_t threads) {
@@ -261,7 +125,7 @@ BatchFn batch_kernel_for(uint32_t program, uint32_t threads) {
 struct GraphKey {
   const void *descs, *images, *out, *status, *ws;
   uint64_t n, tasks, image_bytes, out_bytes, n_status, ws_bytes;
-  uint32_t program, threads, slab, grid;
+  uint32_t program, threads, slab, grid;  // grid: resident CTAs per SM
   bool operator==(const GraphKey &o) const { return std::memcmp(this, &o, sizeof(*this)) == 0; }
 };
 
@@ -357,46 +221,56 @@ struct BatchCall {
   uint64_t ws_bytes;
 };
 
-int32_t resolve_tuning(dsr_ctx *ctx, const BatchCall &c, const dsr_batch_tuning *t_in,
-                       uint32_t *threads, uint32_t *slab, uint32_t *grid) {
-  dsr_batch_tuning t = {256, 16384, 0, 0};
-  if (t_in) t = *t_in;
-  if (t.threads < 64 || t.threads > DSR_MAX_THREADS || t.threads % 32)
+// The CTA shape of a tuning (NULL: 256 threads, 16 KiB), checked.
+int32_t check_tuning(dsr_ctx *ctx, const dsr_batch_tuning *t_in, dsr_batch_tuning *t) {
+  *t = {256, 16384, 0, 0};
+  if (t_in) *t = *t_in;
+  if (t->threads < 64 || t->threads > DSR_MAX_THREADS || t->threads % 32)
     return dsr_fail(ctx, DSR_ERR_INVALID, "batch threads must be a multiple of 32 in [64, 1024]");
-  if (t.slab_bytes % 16 || kCtrlBytes + t.slab_bytes > static_cast<uint32_t>(ctx->max_smem_optin))
+  if (t->slab_bytes % 16 ||
+      kCtrlBytes + t->slab_bytes > static_cast<uint32_t>(ctx->max_smem_optin))
     return dsr_fail(ctx, DSR_ERR_INVALID, "batch slab must be a multiple of 16 fitting a CTA");
-  BatchFn k = batch_kernel_for(c.program, t.threads);
-  if (!k) return dsr_fail(ctx, DSR_ERR_INVALID, "unknown program %u", c.program);
+  return DSR_OK;
+}
+
+// Resident CTAs per SM of a built-in program's persistent kernel in the
+// tuning's shape (capped by the tuning's ctas_per_sm).
+int32_t builtin_per_sm(dsr_ctx *ctx, uint32_t program, const dsr_batch_tuning &t,
+                       uint32_t *per_sm) {
+  BatchFn k = batch_kernel_for(program, t.threads);
+  if (!k) return dsr_fail(ctx, DSR_ERR_INVALID, "unknown program %u", program);
   int occ = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       &occ, reinterpret_cast<const void *>(k), static_cast<int>(t.threads),
       kCtrlBytes + t.slab_bytes);
   if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "occupancy query");
-  if (occ < 1) return dsr_fail(ctx, DSR_ERR_INVALID, "batch CTA shape does not fit an SM");
-  const uint32_t per_sm = t.ctas_per_sm ? std::min<uint32_t>(t.ctas_per_sm, occ) : occ;
-  uint64_t g = static_cast<uint64_t>(ctx->sm_count) * per_sm;
-  g = std::min<uint64_t>(g, std::max<uint64_t>(c.tasks, 1));
-  if (ctx->ovf_per_team) g = std::min<uint64_t>(g, ctx->max_teams);
-  *threads = t.threads;
-  *slab = t.slab_bytes;
-  *grid = static_cast<uint32_t>(std::max<uint64_t>(g, 1));
+  *per_sm = t.ctas_per_sm ? std::min<uint32_t>(t.ctas_per_sm, occ) : static_cast<uint32_t>(occ);
   return DSR_OK;
 }
 
-int32_t enqueue_batch(dsr_ctx *ctx, const BatchCall &c, uint32_t threads, uint32_t slab,
-                      uint32_t grid, cudaStream_t s) {
+// Checks a batch, enqueues its scan and task-list expansion on s, and fills
+// the persistent kernel's plan (grid: per_sm CTAs on every SM, at most one
+// per task and one per overflow slab of the pool).
+int32_t prepare(dsr_ctx *ctx, const BatchCall &c, uint32_t threads, uint32_t slab,
+                uint32_t per_sm, cudaStream_t s, dsr_batch_plan *plan) {
+  if (per_sm < 1) return dsr_fail(ctx, DSR_ERR_INVALID, "batch CTA shape does not fit an SM");
+  uint64_t g = static_cast<uint64_t>(ctx->sm_count) * per_sm;
+  g = std::min<uint64_t>(g, std::max<uint64_t>(c.tasks, 1));
+  if (ctx->ovf_per_team) g = std::min<uint64_t>(g, ctx->max_teams);
   uint8_t *ws = static_cast<uint8_t *>(c.ws);
   WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
   auto *tasks = reinterpret_cast<uint2 *>(ws + ws_tasks_off(c.n));
   batch_scan<<<1, 1024, 0, s>>>(c.descs, c.n, hdr);
   const uint32_t blocks = std::max<uint32_t>(1, std::min<uint32_t>((c.n + 7) / 8, 4096));
-  batch_expand<<<blocks, 256, 0, s>>>(c.descs, c.n, hdr, tasks, c.tasks);
-  BatchArgs a;
+  batch_expand<<<blocks, 256, 0, s>>>(c.descs, c.n, hdr, tasks, c.tasks, c.status, c.n_status);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "batch scan launch");
+  dsr_batch_plan &a = *plan;
   a.descs = c.descs;
   a.tasks = tasks;
   a.hdr = hdr;
-  a.images = static_cast<const uint8_t *>(c.images);
-  a.out = static_cast<uint8_t *>(c.out);
+  a.images = c.images;
+  a.out = c.out;
   a.status = c.status;
   a.pool = ctx->pool;
   a.capacity = c.tasks;
@@ -407,25 +281,61 @@ int32_t enqueue_batch(dsr_ctx *ctx, const BatchCall &c, uint32_t threads, uint32
   a.timeout_ns = ctx->timeout_ns;
   a.n = c.n;
   a.slab_bytes = slab;
-  batch_kernel_for(c.program, threads)<<<grid, threads, kCtrlBytes + slab, s>>>(a);
+  a.grid = static_cast<uint32_t>(std::max<uint64_t>(g, 1));
+  a.threads = threads;
+  return DSR_OK;
+}
+
+// A whole batch of a built-in program: prepare, then the persistent kernel.
+int32_t enqueue_batch(dsr_ctx *ctx, const BatchCall &c, const dsr_batch_tuning &t,
+                      uint32_t per_sm, cudaStream_t s) {
+  dsr_batch_plan a;
+  int32_t rc = prepare(ctx, c, t.threads, t.slab_bytes, per_sm, s, &a);
+  if (rc != DSR_OK) return rc;
+  batch_kernel_for(c.program, a.threads)<<<a.grid, a.threads, kCtrlBytes + a.slab_bytes, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "batch launch");
   return DSR_OK;
 }
 
-int32_t check_batch(dsr_ctx *ctx, const BatchCall &c) {
+// Arguments every batched entry point checks, the workspace aside.
+int32_t check_batch_args(dsr_ctx *ctx, const BatchCall &c) {
   if (!ctx) return dsr_fail(nullptr, DSR_ERR_INVALID, "null ctx");
   if (!ctx->stack_ready) return dsr_fail(ctx, DSR_ERR_INVALID, "dsr_stack_init not called");
-  if (!c.descs || c.n == 0 || !c.out || !c.status || !c.ws)
+  int32_t rc = dsr_check_device(ctx);
+  if (rc != DSR_OK) return rc;
+  if (!c.descs || c.n == 0 || !c.out || !c.status)
     return dsr_fail(ctx, DSR_ERR_INVALID, "null batch argument or empty batch");
-  if ((reinterpret_cast<uintptr_t>(c.descs) | reinterpret_cast<uintptr_t>(c.ws)) & 15u)
-    return dsr_fail(ctx, DSR_ERR_INVALID, "descriptors and workspace must be 16-byte aligned");
+  if (reinterpret_cast<uintptr_t>(c.descs) & 15u)
+    return dsr_fail(ctx, DSR_ERR_INVALID, "descriptors must be 16-byte aligned");
   if (c.tasks >= 0xffffffffull)
     return dsr_fail(ctx, DSR_ERR_INVALID, "a batch holds fewer than 2^32 - 1 teams");
+  return DSR_OK;
+}
+
+int32_t check_batch(dsr_ctx *ctx, const BatchCall &c) {
+  int32_t rc = check_batch_args(ctx, c);
+  if (rc != DSR_OK) return rc;
+  if (!c.ws) return dsr_fail(ctx, DSR_ERR_INVALID, "null workspace");
+  if (reinterpret_cast<uintptr_t>(c.ws) & 15u)
+    return dsr_fail(ctx, DSR_ERR_INVALID, "workspace must be 16-byte aligned");
   if (c.ws_bytes < ws_bytes(c.n, c.tasks))
     return dsr_fail(ctx, DSR_ERR_BUDGET, "workspace of %llu bytes, %llu needed",
                     (unsigned long long)c.ws_bytes, (unsigned long long)ws_bytes(c.n, c.tasks));
-  return set_batch_attrs(ctx);
+  return DSR_OK;
+}
+
+// Check, tuning and resident CTAs of a built-in program's batch.
+int32_t builtin_setup(dsr_ctx *ctx, const BatchCall &c, const dsr_batch_tuning *t_in,
+                      dsr_batch_tuning *t, uint32_t *per_sm) {
+  if (c.program >= DSR_PROG_USER)
+    return dsr_fail(ctx, DSR_ERR_INVALID,
+                    "program %u is user-written: launch it with dsr_launch_user_batch",
+                    c.program);
+  int32_t rc = check_tuning(ctx, t_in, t);
+  if (rc == DSR_OK) rc = set_batch_attrs(ctx);
+  if (rc == DSR_OK) rc = builtin_per_sm(ctx, c.program, *t, per_sm);
+  return rc;
 }
 
 }  // namespace
@@ -441,10 +351,11 @@ extern "C" int32_t dsr_launch_batch(dsr_ctx *ctx, const dsr_region_desc *descs_d
               out_bytes, status_dev, n_status, workspace_dev, workspace_bytes};
   int32_t rc = check_batch(ctx, c);
   if (rc != DSR_OK) return rc;
-  uint32_t threads, slab, grid;
-  if ((rc = resolve_tuning(ctx, c, tuning, &threads, &slab, &grid)) != DSR_OK) return rc;
+  dsr_batch_tuning t;
+  uint32_t per_sm = 0;
+  if ((rc = builtin_setup(ctx, c, tuning, &t, &per_sm)) != DSR_OK) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (!use_graph) return enqueue_batch(ctx, c, threads, slab, grid, s);
+  if (!use_graph) return enqueue_batch(ctx, c, t, per_sm, s);
 
   dsr_batch_state *b = batch_state(ctx);
   GraphKey key;
@@ -461,9 +372,9 @@ extern "C" int32_t dsr_launch_batch(dsr_ctx *ctx, const dsr_region_desc *descs_d
   key.n_status = n_status;
   key.ws_bytes = workspace_bytes;
   key.program = program;
-  key.threads = threads;
-  key.slab = slab;
-  key.grid = grid;
+  key.threads = t.threads;
+  key.slab = t.slab_bytes;
+  key.grid = per_sm;
   cudaGraphExec_t exec = nullptr;
   for (auto &g : b->graphs)
     if (g.key == key) exec = g.exec;
@@ -474,7 +385,7 @@ extern "C" int32_t dsr_launch_batch(dsr_ctx *ctx, const dsr_region_desc *descs_d
       return dsr_cuda_fail(ctx, e, "capture stream");
     if ((e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
       return dsr_cuda_fail(ctx, e, "begin capture");
-    rc = enqueue_batch(ctx, c, threads, slab, grid, b->capture);
+    rc = enqueue_batch(ctx, c, t, per_sm, b->capture);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(b->capture, &graph);
     if (rc != DSR_OK) {
@@ -531,14 +442,15 @@ extern "C" int32_t dsr_autotune(dsr_ctx *ctx, const dsr_region_desc *descs_dev, 
   const uint32_t kSlabs[] = {2048, 4096, 8192, 16384, 32768};
   for (uint32_t th : kThreads)
     for (uint32_t sl : kSlabs) {
-      dsr_batch_tuning t = {th, sl, 0, 0};
-      uint32_t threads, slab, grid;
-      if (resolve_tuning(ctx, c, &t, &threads, &slab, &grid) != DSR_OK) continue;
-      if (enqueue_batch(ctx, c, threads, slab, grid, s) != DSR_OK) continue;  // warm
+      const dsr_batch_tuning cand = {th, sl, 0, 0};
+      dsr_batch_tuning t;
+      uint32_t per_sm = 0;
+      if (builtin_setup(ctx, c, &cand, &t, &per_sm) != DSR_OK) continue;
+      if (enqueue_batch(ctx, c, t, per_sm, s) != DSR_OK) continue;  // warm
       float ms = 1e30f;
       for (int rep = 0; rep < 2; ++rep) {
         cudaEventRecord(a, s);
-        enqueue_batch(ctx, c, threads, slab, grid, s);
+        enqueue_batch(ctx, c, t, per_sm, s);
         cudaEventRecord(z, s);
         cudaEventSynchronize(z);
         float m = 0;
@@ -591,39 +503,21 @@ static __device__ __align__(256) uint8_t g_static_ws[kStaticWsBytes];
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
-void *g_static_ptr[kMaxDevices];      // device address of g_static_ws, per device
-bool g_static_attrs[kMaxDevices];     // batch kernels' shared-memory limit set
+void *g_static_ptr[kMaxDevices];  // device address of g_static_ws, per device
 
-// Once per device, with that device current: the array's device address
-// (the host-side symbol is only a stand-in for it) and the batch kernels'
-// dynamic shared-memory limit.
+// Once per device, with that device current (every entry point requires the
+// ctx's device to be current): the array's device address, for the host-side
+// symbol is only a stand-in for it. The batch kernels' shared-memory limit
+// is set per ctx, as for every batched launch.
 int32_t static_setup(dsr_ctx *ctx, void **ws) {
   if (ctx->device < 0 || ctx->device >= kMaxDevices)
     return dsr_fail(ctx, DSR_ERR_INVALID, "device ordinal out of range");
   std::lock_guard<std::mutex> g(g_static_mu);
-  if (!g_static_ptr[ctx->device] || !g_static_attrs[ctx->device]) {
-    int cur = -1;
-    cudaError_t e = cudaGetDevice(&cur);
-    if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "cudaGetDevice");
-    if (cur != ctx->device && (e = cudaSetDevice(ctx->device)) != cudaSuccess)
-      return dsr_cuda_fail(ctx, e, "cudaSetDevice");
+  if (!g_static_ptr[ctx->device]) {
     void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_ws);
-    if (e == cudaSuccess)
-      for (uint32_t prog = DSR_PROG_PAPER_SCALARS; prog <= DSR_PROG_HETERO && e == cudaSuccess; ++prog)
-        for (uint32_t t : {128u, 256u, 1024u}) {
-          const void *k = reinterpret_cast<const void *>(batch_kernel_for(prog, t));
-          e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   ctx->max_smem_optin);
-          if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     cudaSharedmemCarveoutMaxShared);
-          if (e != cudaSuccess) break;
-        }
-    if (cur != ctx->device) cudaSetDevice(cur);
-    if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "static workspace set-up");
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_ws);
+    if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "static workspace address");
     g_static_ptr[ctx->device] = p;
-    g_static_attrs[ctx->device] = true;
   }
   *ws = g_static_ptr[ctx->device];
   return DSR_OK;
@@ -638,25 +532,59 @@ extern "C" int32_t dsr_launch_batch_static(dsr_ctx *ctx, const dsr_region_desc *
                                            void *out_dev, uint64_t out_bytes,
                                            dsr_team_status *status_dev, uint64_t n_status,
                                            const dsr_batch_tuning *tuning, void *stream) {
-  if (!ctx) return dsr_fail(nullptr, DSR_ERR_INVALID, "null ctx");
-  if (!ctx->stack_ready) return dsr_fail(ctx, DSR_ERR_INVALID, "dsr_stack_init not called");
-  if (!descs_dev || n == 0 || !out_dev || !status_dev)
-    return dsr_fail(ctx, DSR_ERR_INVALID, "null batch argument or empty batch");
-  if (reinterpret_cast<uintptr_t>(descs_dev) & 15u)
-    return dsr_fail(ctx, DSR_ERR_INVALID, "descriptors must be 16-byte aligned");
-  if (total_teams >= 0xffffffffull || ws_bytes(n, total_teams) > kStaticWsBytes)
+  BatchCall c{descs_dev, n, program, total_teams, images_dev, image_bytes, out_dev,
+              out_bytes, status_dev, n_status, nullptr, kStaticWsBytes};
+  int32_t rc = check_batch_args(ctx, c);
+  if (rc != DSR_OK) return rc;
+  if (ws_bytes(n, total_teams) > kStaticWsBytes)
     return dsr_fail(ctx, DSR_ERR_BUDGET,
                     "a batch of %llu teams needs %llu workspace bytes; the static workspace "
                     "holds %llu (use dsr_launch_batch with a caller buffer)",
                     (unsigned long long)total_teams,
                     (unsigned long long)ws_bytes(n, total_teams),
                     (unsigned long long)kStaticWsBytes);
-  void *ws = nullptr;
-  int32_t rc = static_setup(ctx, &ws);
+  if ((rc = static_setup(ctx, &c.ws)) != DSR_OK) return rc;
+  dsr_batch_tuning t;
+  uint32_t per_sm = 0;
+  if ((rc = builtin_setup(ctx, c, tuning, &t, &per_sm)) != DSR_OK) return rc;
+  return enqueue_batch(ctx, c, t, per_sm, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int32_t dsr_batch_static_errors(dsr_ctx *ctx, uint32_t *errors,
+                                           uint64_t *tasks_counted, void *stream) {
+  if (!ctx || !errors) return dsr_fail(ctx, DSR_ERR_INVALID, "null argument");
+  int32_t rc = dsr_check_device(ctx);
   if (rc != DSR_OK) return rc;
+  void *ws = nullptr;
+  {
+    std::lock_guard<std::mutex> g(g_static_mu);
+    if (ctx->device >= 0 && ctx->device < kMaxDevices) ws = g_static_ptr[ctx->device];
+  }
+  if (!ws) return dsr_fail(ctx, DSR_ERR_INVALID, "no static batch has run on this device");
+  return dsr_batch_errors(ctx, ws, errors, tasks_counted, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Batches of user-written programs (dsr_device.cuh): the library checks the
+// batch, enqueues its scan and task list, and returns the plan the user's
+// translation unit launches its own instance of the persistent kernel with.
+// ---------------------------------------------------------------------------
+extern "C" int32_t dsr_batch_prepare(dsr_ctx *ctx, const dsr_region_desc *descs_dev, uint32_t n,
+                                     uint32_t program, uint64_t total_teams,
+                                     const void *images_dev, uint64_t image_bytes, void *out_dev,
+                                     uint64_t out_bytes, dsr_team_status *status_dev,
+                                     uint64_t n_status, void *workspace_dev,
+                                     uint64_t workspace_bytes, uint32_t threads,
+                                     uint32_t slab_bytes, uint32_t ctas_per_sm, void *stream,
+                                     dsr_batch_plan *plan) {
+  if (!plan) return dsr_fail(ctx, DSR_ERR_INVALID, "null plan");
   BatchCall c{descs_dev, n, program, total_teams, images_dev, image_bytes, out_dev,
-              out_bytes, status_dev, n_status, ws, kStaticWsBytes};
-  uint32_t threads, slab, grid;
-  if ((rc = resolve_tuning(ctx, c, tuning, &threads, &slab, &grid)) != DSR_OK) return rc;
-  return enqueue_batch(ctx, c, threads, slab, grid, static_cast<cudaStream_t>(stream));
+              out_bytes, status_dev, n_status, workspace_dev, workspace_bytes};
+  int32_t rc = check_batch(ctx, c);
+  if (rc != DSR_OK) return rc;
+  const dsr_batch_tuning in = {threads, slab_bytes, 0, 0};
+  dsr_batch_tuning t;
+  if ((rc = check_tuning(ctx, &in, &t)) != DSR_OK) return rc;
+  return prepare(ctx, c, t.threads, t.slab_bytes, ctas_per_sm, static_cast<cudaStream_t>(stream),
+                 plan);
 }

@@ -1,5 +1,7 @@
 // dsr_capi.cu -- plain per-region launch and the host side of the C ABI:
-// context, stack configuration, descriptor checks, footprint model.
+// context, stack configuration, descriptor checks, footprint model. The
+// plain kernel itself (plain_kernel in dsr_kernels.cuh) is a template over
+// the program, shared with programs written against dsr_device.cuh.
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -12,76 +14,24 @@
 #include "dsr.h"
 #include "dsr_check.cuh"
 #include "dsr_ctx.h"
+#include "dsr_kernels.cuh"
 #include "dsr_programs.cuh"
 
 using namespace dsr;
 
-// ---------------------------------------------------------------------------
-// Plain kernel: one CTA per team (Sec. 4: a target region compiles to one
-// kernel with a fixed number of teams and threads; team = threadblock).
-// MAXT/MINB bound the registers so that teams of MAXT threads can reach
-// MINB resident CTAs per SM.
-// ---------------------------------------------------------------------------
-template <class P, int MAXT, int MINB>
-__global__ void __launch_bounds__(MAXT, MINB)
-    plain_kernel(const __grid_constant__ dsr_region_desc d, const uint8_t *__restrict__ images,
-                 uint8_t *__restrict__ out, dsr_team_status *__restrict__ st,
-                 uint8_t *__restrict__ pool, uint64_t ovf_per_team, uint32_t slab_bytes,
-                 uint64_t timeout_ns) {
-  Env e;
-  e.d = &d;
-  e.images = images;
-  e.out = out;
-  e.team = blockIdx.x;
-  if (threadIdx.x == 0) signal_dependents();
-  if (threadIdx.x < team_workers()) {
-    wait_prerequisites();
-    worker_loop<P>(e);
-    return;
-  }
-  Stack s;
-  team_setup(s, slab_bytes,
-             ovf_per_team ? pool + static_cast<uint64_t>(blockIdx.x) * ovf_per_team : nullptr,
-             ovf_per_team, timeout_ns, true);
-  wait_prerequisites();  // the set-up above touches shared memory only
-  P::master(e, s);
-  terminate_workers();
-  team_report(e, s, st);
-}
-
 namespace {
 
-using KernelFn = void (*)(dsr_region_desc, const uint8_t *, uint8_t *, dsr_team_status *,
-                          uint8_t *, uint64_t, uint32_t, uint64_t);
-
-// Programs whose launches fill the GPU with many teams (P::kDense) are
-// held to 32 registers, so 2048 threads per SM can be resident; those whose
-// teams are few per SM anyway (wide_regs) get up to 85; the others 64.
-template <class P, class = void>
-struct wide_regs : std::false_type {};
-template <class P>
-struct wide_regs<P, std::void_t<decltype(P::kWideRegs)>> : std::bool_constant<P::kWideRegs> {};
-
-template <class P>
-KernelFn pick(uint32_t threads) {
-  // resident CTAs of 256 threads the register budget is sized for
-  constexpr int k = P::kDense ? 8 : wide_regs<P>::value ? 3 : 4;
-  if (threads <= 128) return plain_kernel<P, 128, 2 * k>;
-  if (threads <= 256) return plain_kernel<P, 256, k>;
-  constexpr int k512 = k / 2 > 1 ? k / 2 : 1, k1024 = k / 4 > 1 ? k / 4 : 1;
-  if (threads <= 512) return plain_kernel<P, 512, k512>;
-  return plain_kernel<P, 1024, k1024>;
-}
+using KernelFn = PlainFn;
 
 KernelFn plain_kernel_for(uint32_t program, uint32_t threads) {
   switch (program) {
-    case DSR_PROG_PAPER_SCALARS: return pick<ProgPaperScalars>(threads);
-    case DSR_PROG_PAPER_ARRAYS: return pick<ProgPaperArrays>(threads);
-    case DSR_PROG_SCALARS: return pick<ProgScalars>(threads);
-    case DSR_PROG_NESTED: return pick<ProgNested>(threads);
-    case DSR_PROG_SWEEP: return pick<ProgSweep>(threads);
-    case DSR_PROG_HETERO: return pick<ProgHetero>(threads);
-    case DSR_PROG_WORKERS: return pick<ProgWorkers>(threads);
+    case DSR_PROG_PAPER_SCALARS: return pick_plain<ProgPaperScalars>(threads);
+    case DSR_PROG_PAPER_ARRAYS: return pick_plain<ProgPaperArrays>(threads);
+    case DSR_PROG_SCALARS: return pick_plain<ProgScalars>(threads);
+    case DSR_PROG_NESTED: return pick_plain<ProgNested>(threads);
+    case DSR_PROG_SWEEP: return pick_plain<ProgSweep>(threads);
+    case DSR_PROG_HETERO: return pick_plain<ProgHetero>(threads);
+    case DSR_PROG_WORKERS: return pick_plain<ProgWorkers>(threads);
     default: return nullptr;
   }
 }
@@ -108,6 +58,22 @@ int32_t dsr_fail(dsr_ctx *ctx, int32_t code, const char *fmt, ...) {
 
 int32_t dsr_cuda_fail(dsr_ctx *ctx, cudaError_t e, const char *what) {
   return dsr_fail(ctx, DSR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int32_t dsr_check_device(dsr_ctx *ctx) {
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "cudaGetDevice");
+  if (cur != ctx->device)
+    return dsr_fail(ctx, DSR_ERR_INVALID,
+                    "the calling thread's current device is %d, the context's is %d "
+                    "(cudaSetDevice(%d) first)",
+                    cur, ctx->device, ctx->device);
+  return DSR_OK;
+}
+
+extern "C" int32_t dsr_report_error(dsr_ctx *ctx, int32_t code, const char *msg) {
+  return dsr_fail(ctx, code, "%s", msg ? msg : "");
 }
 
 extern "C" const char *dsr_last_error_string(const dsr_ctx *ctx) {
@@ -347,16 +313,66 @@ int32_t dsr_launch_plain(dsr_ctx *ctx, const dsr_region_desc *d, const void *ima
   return DSR_OK;
 }
 
-static int32_t check_launch(dsr_ctx *ctx, const dsr_region_desc *d, const void *out_dev,
-                            const void *status_dev) {
+// Checks every plain launch makes, built-in or user-written program.
+static int32_t check_launch_common(dsr_ctx *ctx, const dsr_region_desc *d, const void *out_dev,
+                                   const void *status_dev) {
   if (!ctx) return dsr_fail(nullptr, DSR_ERR_INVALID, "null ctx");
   if (!ctx->stack_ready) return dsr_fail(ctx, DSR_ERR_INVALID, "dsr_stack_init not called");
+  int32_t rc = dsr_check_device(ctx);
+  if (rc != DSR_OK) return rc;
   const char *why;
   if (dsr_check_shape(d, &why) != DSR_OK) return dsr_fail(ctx, DSR_ERR_INVALID, "%s", why);
   if (!out_dev || !status_dev) return dsr_fail(ctx, DSR_ERR_INVALID, "null output or status");
   if (ctx->ovf_per_team && d->teams > ctx->max_teams)
     return dsr_fail(ctx, DSR_ERR_BUDGET, "%u teams exceed the %u overflow slabs", d->teams,
                     ctx->max_teams);
+  return DSR_OK;
+}
+
+static int32_t check_launch(dsr_ctx *ctx, const dsr_region_desc *d, const void *out_dev,
+                            const void *status_dev) {
+  int32_t rc = check_launch_common(ctx, d, out_dev, status_dev);
+  if (rc == DSR_OK && d->program >= DSR_PROG_USER)
+    return dsr_fail(ctx, DSR_ERR_INVALID,
+                    "program %u is user-written: launch it with dsr_launch_user_region",
+                    d->program);
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Plain launches of user-written programs (dsr_device.cuh): the checks and
+// the ctx's stack configuration; the user's translation unit launches its
+// own instance of the plain kernel with them.
+// ---------------------------------------------------------------------------
+extern "C" int32_t dsr_user_plain_config(dsr_ctx *ctx, const dsr_region_desc *d,
+                                         uint64_t image_need, uint64_t out_need,
+                                         uint64_t image_bytes, uint64_t out_bytes,
+                                         uint64_t n_status, const void *out_dev,
+                                         const void *status_dev, dsr_plain_config *cfg) {
+  if (!cfg) return dsr_fail(ctx, DSR_ERR_INVALID, "null output");
+  int32_t rc = check_launch_common(ctx, d, out_dev, status_dev);
+  if (rc != DSR_OK) return rc;
+  if (d->program < DSR_PROG_USER)
+    return dsr_fail(ctx, DSR_ERR_INVALID, "program %u is built in: use dsr_launch_region",
+                    d->program);
+  if (image_need && (d->image_offset > image_bytes || image_need > image_bytes - d->image_offset))
+    return dsr_fail(ctx, DSR_ERR_INVALID, "region needs images [%llu, +%llu) of %llu",
+                    (unsigned long long)d->image_offset, (unsigned long long)image_need,
+                    (unsigned long long)image_bytes);
+  if (d->out_offset > out_bytes || out_need > out_bytes - d->out_offset)
+    return dsr_fail(ctx, DSR_ERR_INVALID, "region needs outputs [%llu, +%llu) of %llu",
+                    (unsigned long long)d->out_offset, (unsigned long long)out_need,
+                    (unsigned long long)out_bytes);
+  if (static_cast<uint64_t>(d->status_index) + d->teams > n_status)
+    return dsr_fail(ctx, DSR_ERR_INVALID, "region needs statuses [%u, +%u) of %llu",
+                    d->status_index, d->teams, (unsigned long long)n_status);
+  cfg->pool_dev = ctx->pool;
+  cfg->ovf_per_team = ctx->ovf_per_team;
+  cfg->timeout_ns = ctx->timeout_ns;
+  cfg->slab_bytes = dsr_plain_slab(ctx, d);
+  cfg->ctrl_bytes = kCtrlBytes;
+  cfg->device = ctx->device;
+  cfg->max_smem = static_cast<uint32_t>(ctx->max_smem_optin);
   return DSR_OK;
 }
 

@@ -34,6 +34,9 @@ struct dsr_ctx {
 // Record an error on ctx (and process-wide); returns `code`.
 int32_t dsr_fail(dsr_ctx *ctx, int32_t code, const char *fmt, ...);
 int32_t dsr_cuda_fail(dsr_ctx *ctx, cudaError_t e, const char *what);
+// DSR_OK when the calling thread's current device is the ctx's; otherwise
+// DSR_ERR_INVALID (a launch would run on another GPU than the ctx's pool).
+int32_t dsr_check_device(dsr_ctx *ctx);
 // Descriptor shape checks shared by every launch form.
 int32_t dsr_check_shape(const dsr_region_desc *d, const char **why);
 // Slab of a plain launch of *d: the configured slab, or with DSR_SLAB_AUTO

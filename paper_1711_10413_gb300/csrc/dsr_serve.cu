@@ -592,6 +592,7 @@ extern "C" int32_t dsr_serve_start(dsr_ctx *ctx, const dsr_serve_cfg *cfg, void 
                                    uint64_t workspace_bytes) {
   if (!ctx || !cfg) return dsr_fail(ctx, DSR_ERR_INVALID, "null argument");
   if (!ctx->stack_ready) return dsr_fail(ctx, DSR_ERR_INVALID, "dsr_stack_init not called");
+  if (int32_t rc = dsr_check_device(ctx)) return rc;
   if (ctx->serve && ctx->serve->running) return dsr_fail(ctx, DSR_ERR_INVALID, "already serving");
   if (!serve_kernel_for(cfg->program, cfg->threads))
     return dsr_fail(ctx, DSR_ERR_INVALID, "the served form runs the scalars, nested and hetero programs");

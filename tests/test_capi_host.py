@@ -165,3 +165,33 @@ def test_bounded_wait_check_rejects_missing_context(L):
 
 def test_stack_check_rejects_bad_arguments(L):
     assert L.dsr_check_stack(None, None, 0, None, 0, None) == dsr.DSR_ERR_INVALID
+
+
+def test_report_error_records_the_message(L):
+    """dsr_report_error: the way code built on the library (the launch
+    templates of dsr_device.cuh) reports a failure; no ctx needed."""
+    assert dsr.dsr_report_error(None, dsr.DSR_ERR_BUDGET, "pool too small for x") == 4
+    assert dsr.lib().dsr_last_error_string(None).decode() == "pool too small for x"
+
+
+def test_user_program_library_builds_and_exports(L):
+    """A program written against include/dsr_device.cuh compiles (nvcc,
+    sm_103a) into its own library linked with libdsr, exporting the test
+    programs' entry points; descriptors naming a user program id pass the
+    host-side shape check with no extent of their own."""
+    import ctypes
+    src = os.path.join(ROOT, "tests", "user_program", "user_programs.cu")
+    out = os.path.join(ROOT, "tests", "user_program", "libuser_programs.so")
+    dsr_build.build_user([src], out)
+    U = ctypes.CDLL(out)
+    for name in ("user_paper_scalars", "user_hetero"):
+        for suffix in ("_launch", "_launch_batch", "_program"):
+            assert hasattr(U, name + suffix)
+    U.user_hetero_program.restype = ctypes.c_uint32
+    assert U.user_hetero_program() == dsr.DSR_PROG_USER + 6
+    r = wl.hetero(n_instances=1, max_teams=4, max_frame=256).regions[0]
+    r.program = dsr.DSR_PROG_USER + 6
+    assert dsr.dsr_region_extent(r) == (0, 0, r.teams)
+    r.program = 200   # neither built in nor in the user range
+    with pytest.raises(dsr.DsrError):
+        dsr.dsr_region_extent(r)

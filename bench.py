@@ -339,10 +339,35 @@ def smem_footprint(torch, rt, region, device):
                               "of the 16 KB default shared memory (Sec. 6.3)")
 
 
-def smem_peak_gbs(sm_count: int, sm_mhz: float = 2070.0) -> float:
-    """Shared-memory bandwidth bound: 128 bytes per clock per SM (32 banks
-    of 4 bytes) at the maximum SM clock."""
+def smem_derived_gbs(sm_count: int, sm_mhz: float = 2070.0) -> float:
+    """Shared-memory bandwidth from the unit counts: 128 bytes per clock per
+    SM (32 banks of 4 bytes) at the maximum SM clock."""
     return sm_count * 128.0 * sm_mhz * 1e6 / 1e9
+
+
+_SMEM_PEAK = {}
+
+
+def smem_peak(dsr=None, torch=None, device: int = 0, sm_count: int = 152) -> dict:
+    """The shared-memory roofline: measured once per run by the library's
+    probe (conflict-free 16-byte loads streaming on every SM, CUDA-event
+    timed), with the figure derived from the unit counts beside it."""
+    if "gbs" not in _SMEM_PEAK:
+        derived = smem_derived_gbs(sm_count)
+        try:
+            rt = dsr.Runtime(device, slab_bytes=0)
+            scratch = torch.zeros(4, dtype=torch.int64, device="cuda:%d" % device)
+            p = dsr.dsr_probe_smem_bandwidth(rt.ctx, 4096, scratch)
+            rt.close()
+            _SMEM_PEAK.update(gbs=p["gbs"], source="measured", probe=p, derived_gbs=derived)
+        except Exception as e:   # noqa: BLE001 - a probe failure must not hide the bench
+            _SMEM_PEAK.update(gbs=derived, source="derived (probe failed: %s)" % e,
+                              derived_gbs=derived)
+    return _SMEM_PEAK
+
+
+def smem_peak_gbs(sm_count: int) -> float:
+    return smem_peak(sm_count=sm_count)["gbs"] if _SMEM_PEAK else smem_derived_gbs(sm_count)
 
 
 def hetero_stack_bytes(regions) -> int:
@@ -369,7 +394,7 @@ def measure_sweep(dsr, torch, device, flush, hbm_gbs, sizes=None):
     copies launched back to back; smaller ones one launch at a time after
     an L2 flush."""
     teams, threads = 512, 128
-    smem_peak = smem_peak_gbs(torch.cuda.get_device_properties(device).multi_processor_count)
+    smem_bound = smem_peak_gbs(torch.cuda.get_device_properties(device).multi_processor_count)
     rt = dsr.Runtime(device, slab_bytes=0, overflow_bytes_per_team=max(wl.SWEEP_SIZES),
                      max_teams=teams)
     res = []
@@ -414,7 +439,7 @@ def measure_sweep(dsr, torch, device, flush, hbm_gbs, sizes=None):
             res.append(dict(frame_bytes=S, placement=where, us=ms * 1e3,
                             regions_per_s=1.0 / (ms * 1e-3), hbm_bytes=hbm, hbm_gbs=gbs,
                             hbm_frac=gbs / hbm_gbs, smem_bytes=smem, smem_gbs=smem_gbs,
-                            smem_frac=smem_gbs / smem_peak,
+                            smem_frac=smem_gbs / smem_bound,
                             overflow_bytes=2 * teams * S if where == "overflow" else 0,
                             smem_per_team=occ["smem_per_team"], ctas_per_sm=occ["ctas_per_sm"],
                             regs_per_thread=occ["regs_per_thread"],
@@ -465,6 +490,9 @@ def measure_forms(dsr, torch, device, flush, hbm_gbs, which=FORMS, instances=100
                   sweep_sizes=None, tuning=None):
     forms = {}
     sm_count = torch.cuda.get_device_properties(device).multi_processor_count
+    peak = smem_peak(dsr, torch, device, sm_count)
+    forms["smem_peak"] = dict(gbs=peak["gbs"], source=peak["source"],
+                              derived_gbs=peak["derived_gbs"], probe=peak.get("probe"))
     if "sweep" in which:
         forms["sweep"] = measure_sweep(dsr, torch, device, flush, hbm_gbs, sweep_sizes)
     rt = dsr.Runtime(device, slab_bytes=16384, overflow_bytes_per_team=3 * 32768, max_teams=4096)
@@ -532,8 +560,8 @@ def measure_batched(dsr, torch, rt, flush, sm_count, instances=10000, tuning=Non
                                                 achieved=smem_gbs,
                                                 peak=smem_peak_gbs(sm_count), unit="GB/s",
                                                 frac=smem_gbs / smem_peak_gbs(sm_count),
-                                                peak_source="derived: SMs x 128 B/clk x "
-                                                            "2070 MHz"),
+                                                peak_source=_SMEM_PEAK.get("source", "derived"),
+                                                derived_peak=smem_derived_gbs(sm_count)),
                             device_rejects=err,
                             bad_team_status=int((st["status"] != 0).sum()))
     del b

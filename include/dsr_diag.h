@@ -57,6 +57,31 @@ int32_t dsr_check_bounded_wait(dsr_ctx *ctx, uint64_t timeout_ns, uint64_t *resu
 int32_t dsr_check_stack(dsr_ctx *ctx, uint64_t *result_dev, uint32_t n_result,
                         void *scratch_dev, uint64_t scratch_bytes, void *stream);
 
+/* Measured shared-memory bandwidth of this GPU: the roofline the runtime's
+ * stack traffic (frames written and read in the shared-memory slab, Sec.
+ * 5.3) is reported against. Every SM runs CTAs of 1024 threads (as many as
+ * fit) that stream conflict-free 16-byte loads (ld.shared.v4, a warp
+ * reading 512 consecutive bytes) from a 32 KiB buffer, `reps` rounds of 8
+ * loads per thread; one warm-up launch, then one launch timed with CUDA
+ * events on `stream`. scratch_dev: caller-owned device memory of 4
+ * uint64_t. Synchronises `stream`. out receives the bytes loaded, the
+ * event time, the bandwidth, and the SM clock during the timed launch (the
+ * %clock64 cycles over the %globaltimer nanoseconds of its slowest CTA),
+ * from which the bytes per SM per clock follow. Errors: DSR_ERR_INVALID
+ * (null argument, reps 0 or above 2^20), DSR_ERR_CUDA. */
+typedef struct dsr_smem_probe {
+  uint64_t bytes;           /* shared-memory bytes loaded by the timed launch */
+  double ms;                /* its duration between CUDA events */
+  double gbs;               /* bytes / ms, all SMs */
+  double sm_mhz;            /* SM clock during it */
+  double bytes_per_clk_sm;  /* gbs / (SMs x SM clock) */
+  uint32_t ctas;            /* CTAs of the launch */
+  uint32_t threads;         /* threads per CTA */
+} dsr_smem_probe;
+
+int32_t dsr_probe_smem_bandwidth(dsr_ctx *ctx, uint32_t reps, uint64_t *scratch_dev,
+                                 void *stream, dsr_smem_probe *out);
+
 #ifdef __cplusplus
 }
 #endif

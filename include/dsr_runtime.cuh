@@ -57,7 +57,7 @@ struct __align__(16) Ctrl {
   uint32_t work;      // body id of the current parallel region or kTerminate
   uint32_t nthreads;  // threads of the current parallel region
   uint32_t arg;       // per-region argument (level, region index)
-  uint32_t task;      // batched launch: current task
+  uint32_t acc;       // a wrap-around sum the workers of a region add up (reset by the master)
   uint64_t mbar;      // mbarrier completing bulk-copy fills
   uint64_t timeout_ns;
   uint8_t *ovf;       // this team's overflow slab
@@ -625,23 +625,6 @@ __device__ __forceinline__ void stream_finish(Stack &s) {
   if (!ok) set_status(s, DSR_ERR_TIMEOUT);
   s.bits ^= 0x400u;
   __syncwarp();
-}
-
-// Sum of the words [0, words) of a frame (master warp; wrap-around sum, so
-// the lane split gives the same value as one thread summing in order).
-// 16-byte loads when the frame is 16-byte aligned.
-__device__ __forceinline__ uint32_t frame_sum(const uint32_t *f, uint32_t words) {
-  uint32_t v = 0, w0 = 0;
-  if ((reinterpret_cast<uintptr_t>(f) & 15u) == 0) {
-    const uint4 *f4 = reinterpret_cast<const uint4 *>(f);
-    for (uint32_t i = lane_id(); i < words / 4u; i += 32u) {
-      const uint4 x = f4[i];
-      v += x.x + x.y + x.z + x.w;
-    }
-    w0 = words & ~3u;
-  }
-  for (uint32_t w = w0 + lane_id(); w < words; w += 32u) v += f[w];
-  return warp_sum(v);
 }
 
 // ---------------------------------------------------------------------------

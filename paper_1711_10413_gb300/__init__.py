@@ -83,6 +83,12 @@ class dsr_batch_plan(ctypes.Structure):
                 ("threads", ctypes.c_uint32)]
 
 
+class dsr_smem_probe(ctypes.Structure):
+    _fields_ = [("bytes", ctypes.c_uint64), ("ms", ctypes.c_double), ("gbs", ctypes.c_double),
+                ("sm_mhz", ctypes.c_double), ("bytes_per_clk_sm", ctypes.c_double),
+                ("ctas", ctypes.c_uint32), ("threads", ctypes.c_uint32)]
+
+
 class dsr_footprint(ctypes.Structure):
     _fields_ = [("smem_per_team", ctypes.c_uint32), ("ctrl_bytes", ctypes.c_uint32),
                 ("slab_bytes", ctypes.c_uint32), ("teams_per_sm", ctypes.c_uint32),
@@ -137,6 +143,7 @@ def _declare(L):
                                            _vp, _vp, _vp, _vp]),
         "dsr_check_bounded_wait": (_i32, [_vp, _u64, _vp, _vp]),
         "dsr_check_stack": (_i32, [_vp, _vp, _u32, _vp, _u64, _vp]),
+        "dsr_probe_smem_bandwidth": (_i32, [_vp, _u32, _vp, _vp, P(dsr_smem_probe)]),
         "dsr_batch_workspace_bytes": (_u64, [_u32, _u64]),
         "dsr_batch_count": (_i32, [_vp, _u32, _u64, _u64, _u64, P(_u64)]),
         "dsr_launch_batch": (_i32, [_vp, _vp, _u32, _u32, _u64, _vp, _u64, _vp, _u64, _vp, _u64,
@@ -200,7 +207,7 @@ def exported_symbols():
             "dsr_serve_workspace_bytes", "dsr_serve_start",
             "dsr_serve_submit", "dsr_serve_poll", "dsr_serve_stop", "dsr_serve_stats",
             "dsr_serve_bench", "dsr_launch_bench", "dsr_check_bounded_wait",
-            "dsr_check_stack"]
+            "dsr_check_stack", "dsr_probe_smem_bandwidth"]
 
 
 # ---------------------------------------------------------------------------
@@ -426,6 +433,15 @@ def dsr_batch_static_errors(ctx: int, stream=None):
     _check(lib().dsr_batch_static_errors(ctx, ctypes.byref(e), ctypes.byref(t),
                                          _stream(stream)), ctx)
     return int(e.value), int(t.value)
+
+
+def dsr_probe_smem_bandwidth(ctx: int, reps: int, scratch, stream=None) -> dict:
+    """Measured shared-memory bandwidth (scratch: device tensor of at least
+    32 bytes); synchronises `stream`."""
+    r = dsr_smem_probe()
+    _check(lib().dsr_probe_smem_bandwidth(ctx, reps, _ptr(scratch), _stream(stream),
+                                          ctypes.byref(r)), ctx)
+    return {f: getattr(r, f) for f, _ in dsr_smem_probe._fields_}
 
 
 def dsr_report_error(ctx: int, code: int, msg: str) -> int:

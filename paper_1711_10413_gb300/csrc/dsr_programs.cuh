@@ -145,7 +145,8 @@ struct ProgScalars {
 // int32 arr[256]} filled from image[team][k-1] XOR mix32(team*8 + k), with
 // F_k.s[0] ^= F_{k-1}.s[15] for k > 1, then forks:
 //   k < D: F_k.arr[i] = mix32(F_k.arr[i] + i) for the worker's strided i;
-//          after the join the master stores sum(F_k.arr) in F_k.s[15];
+//          after the join F_k.s[15] = sum(F_k.arr) (the workers add their
+//          new words into s[15], which the master cleared before the fork);
 //   k = D: out[e] = mix32(e ^ sum_m (F_m.arr[j & 255] ^ F_m.s[j & 15])),
 //          e = team*E + j, for every j < E (E = param), each j by one
 //          worker.
@@ -207,7 +208,12 @@ struct ProgNested {
       }
       if (s.status() != DSR_OK) return;
       uint32_t *w = reinterpret_cast<uint32_t *>(f);
-      if (lane_id() == 0 && k > 1) w[0] ^= carry;
+      if (lane_id() == 0) {
+        if (k > 1) w[0] ^= carry;
+        // the workers of an update region add their new words into s[15]
+        // (read by no region before the master sets it to the sum)
+        if (k < D) w[15] = 0;
+      }
       __syncwarp();
       // the last level's word 15 is final here (its region writes only the
       // output); earlier levels record their sums below
@@ -221,10 +227,8 @@ struct ProgNested {
       if (kStaged && k == 1 && D > 1) key_levels(dsr_smem + x0, 1, D, e.team);
       join();
       if (k < D) {
-        carry = frame_sum(reinterpret_cast<const uint32_t *>(f) + 16, 256);
-        if (lane_id() == 0) w[15] = carry;
+        carry = w[15];  // the sum of arr the workers left there
         set_chk(s, k - 1, carry);
-        __syncwarp();
       }
     }
     for (uint32_t k = D; k >= 1; --k) {
@@ -256,9 +260,28 @@ struct ProgNested {
     __syncwarp();
   }
 
+  // Update regions: every worker updates its words of arr and adds the new
+  // values up; a warp reduction and one shared-memory atomic per warp put
+  // the frame's sum into s[15] (wrap-around adds: any order gives the sum
+  // the master would take after the join). Every worker thread runs this,
+  // so each warp's reduction has all its lanes.
   __device__ static void run(const Env &e, uint32_t work, uint32_t first, uint32_t W,
-                             uint32_t n, uint32_t arg) {
-    run_threads<ProgNested>(e, work, first, W, n, arg);
+                             uint32_t n, uint32_t k) {
+    if (work != kUpdate) {
+      run_threads<ProgNested>(e, work, first, W, n, k);
+      return;
+    }
+    uint32_t *f = k & kSmemArg ? reinterpret_cast<uint32_t *>(dsr_smem + (k & ~kSmemArg))
+                               : reinterpret_cast<uint32_t *>(ctrl()->frames[k - 1].ptr);
+    uint32_t *arr = f + 16, part = 0;
+    for (uint32_t v = first; v < n; v += W)
+      for (uint32_t i = v; i < 256u; i += n) {
+        const uint32_t x = mix32(arr[i] + i);
+        arr[i] = x;
+        part += x;
+      }
+    part = warp_sum(part);
+    if (lane_id() == 0 && part) atomicAdd(f + 15, part);
   }
 
   // The innermost region over groups g = tid, tid + n, ... < G of 4
@@ -294,15 +317,8 @@ struct ProgNested {
     }
   }
 
-  __device__ static void body(const Env &e, uint32_t work, uint32_t tid, uint32_t n,
-                              uint32_t k) {
-    if (work == kUpdate) {
-      uint32_t *arr = (k & kSmemArg ? reinterpret_cast<uint32_t *>(dsr_smem + (k & ~kSmemArg))
-                                    : reinterpret_cast<uint32_t *>(ctrl()->frames[k - 1].ptr)) +
-                      16;
-      for (uint32_t i = tid; i < 256u; i += n) arr[i] = mix32(arr[i] + i);
-      return;
-    }
+  // The innermost region (update regions run in run() above).
+  __device__ static void body(const Env &e, uint32_t, uint32_t tid, uint32_t n, uint32_t k) {
     const uint32_t D = e.d->depth, E = e.d->param;
     uint32_t *o = reinterpret_cast<uint32_t *>(e.out + e.d->out_offset) +
                   static_cast<uint64_t>(e.team) * E;
@@ -410,8 +426,9 @@ struct ProgSweep {
 // ---------------------------------------------------------------------------
 // Hetero program (heterogeneous instances): D levels of F_k = int32[L_k] filled from the instance's level
 // images XOR mix32(salt + team*8 + k), F_k[0] ^= c_{k-1} for k > 1, then:
-//   k < D: F_k[w] = mix32(F_k[w] + w) for the worker's strided w; after the
-//          join the master sums F_k into c_k (= chk[k-1]);
+//   k < D: F_k[w] = mix32(F_k[w] + w) for the worker's strided w; c_k =
+//          sum of F_k (= chk[k-1]), added up by the workers as they update
+//          it and read by the master after the join;
 //   k = D: out[team*W' + tid] = sum over m <= D and the worker's strided w
 //          of mix32(F_m[w] ^ (m << 24) ^ w).
 // chk[D-1] = F_D[0]; the frames are popped in reverse order.
@@ -447,11 +464,14 @@ struct ProgHetero {
       expect += (S + 15u) & ~15u;
       if (s.status() != DSR_OK) return;
       img += (S + 15u) & ~15u;
-      if (k > 1 && lane_id() == 0) reinterpret_cast<uint32_t *>(f)[0] ^= c_prev;
+      if (lane_id() == 0) {
+        if (k > 1) reinterpret_cast<uint32_t *>(f)[0] ^= c_prev;
+        if (k < D) ctrl()->acc = 0;  // the update region's workers sum F_k here
+      }
       __syncwarp();
       parallel<ProgHetero>(e, k < D ? kUpdate : kInner, width, k);
       if (k < D) {
-        c_prev = frame_sum(reinterpret_cast<const uint32_t *>(f), S / 4u);
+        c_prev = ctrl()->acc;
         set_chk(s, k - 1, c_prev);
       }
     }
@@ -460,15 +480,26 @@ struct ProgHetero {
   }
 
   // The worker's virtual threads with the frame pointers and sizes read
-  // once per region instead of once per thread.
+  // once per region instead of once per thread. An update region also sums
+  // the frame's new words: per worker, then per warp (a reduction), then
+  // one shared-memory atomic per warp into the control block (wrap-around
+  // adds, so the order does not matter); every worker thread runs this, so
+  // each warp's reduction has all its lanes.
   __device__ static void run(const Env &e, uint32_t work, uint32_t first, uint32_t W,
                              uint32_t n, uint32_t k) {
-    const Ctrl *c = ctrl();
+    Ctrl *c = ctrl();
     if (work == kUpdate) {
       uint32_t *f = reinterpret_cast<uint32_t *>(c->frames[k - 1].ptr);
       const uint32_t L = c->frames[k - 1].bytes / 4u;
+      uint32_t part = 0;
       for (uint32_t v = first; v < n && v < L; v += W)
-        for (uint32_t w = v; w < L; w += n) f[w] = mix32(f[w] + w);
+        for (uint32_t w = v; w < L; w += n) {
+          const uint32_t x = mix32(f[w] + w);
+          f[w] = x;
+          part += x;
+        }
+      part = warp_sum(part);
+      if (lane_id() == 0 && part) atomicAdd(&c->acc, part);
       return;
     }
     const uint32_t *f[DSR_MAX_DEPTH];
@@ -497,23 +528,6 @@ struct ProgHetero {
     for (; v < n; v += W) o[v] = 0u;
   }
 
-  __device__ static void body(const Env &e, uint32_t work, uint32_t tid, uint32_t n,
-                              uint32_t k) {
-    if (work == kUpdate) {
-      uint32_t *f = reinterpret_cast<uint32_t *>(ctrl()->frames[k - 1].ptr);
-      const uint32_t L = ctrl()->frames[k - 1].bytes / 4u;
-      for (uint32_t w = tid; w < L; w += n) f[w] = mix32(f[w] + w);
-      return;
-    }
-    uint32_t acc = 0;
-    for (uint32_t m = 1; m <= k; ++m) {
-      const uint32_t *f = frame_words(m - 1);
-      const uint32_t L = ctrl()->frames[m - 1].bytes / 4u;
-      const uint32_t tag = m << 24;
-      for (uint32_t w = tid; w < L; w += n) acc += mix32(f[w] ^ tag ^ w);
-    }
-    reinterpret_cast<uint32_t *>(e.out + e.d->out_offset)[e.team * n + tid] = acc;
-  }
 };
 
 // ---------------------------------------------------------------------------

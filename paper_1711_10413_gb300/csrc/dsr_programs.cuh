@@ -244,18 +244,20 @@ struct ProgNested {
   }
 
   // XOR level m's slot (1088 bytes from base + 1088 m) with
-  // mix32(team*8 + m + 1), for the levels m0 <= m < m1 (master warp).
+  // mix32(team*8 + m + 1), for the levels m0 <= m < m1 (master warp; the
+  // key is computed once per level).
   __device__ static void key_levels(uint8_t *base, uint32_t m0, uint32_t m1, uint32_t team) {
-    uint4 *v = reinterpret_cast<uint4 *>(base);
-    const uint32_t n = m1 * 68u;  // 1088 / 16 vectors per level
-    for (uint32_t i = m0 * 68u + lane_id(); i < n; i += 32u) {
-      const uint32_t key = mix32(team * 8u + i / 68u + 1u);
-      uint4 x = v[i];
-      x.x ^= key;
-      x.y ^= key;
-      x.z ^= key;
-      x.w ^= key;
-      v[i] = x;
+    for (uint32_t m = m0; m < m1; ++m) {
+      uint4 *v = reinterpret_cast<uint4 *>(base + m * kFrameBytes);
+      const uint32_t key = mix32(team * 8u + m + 1u);
+      for (uint32_t i = lane_id(); i < kFrameBytes / 16u; i += 32u) {
+        uint4 x = v[i];
+        x.x ^= key;
+        x.y ^= key;
+        x.z ^= key;
+        x.w ^= key;
+        v[i] = x;
+      }
     }
     __syncwarp();
   }
@@ -284,36 +286,43 @@ struct ProgNested {
     if (lane_id() == 0 && part) atomicAdd(f + 15, part);
   }
 
-  // The innermost region over groups g = tid, tid + n, ... < G of 4
-  // consecutive elements j0 = 4g .. 4g + 3, with the kD frames back to back
-  // in shared memory from byte `base` on. arr[j & 255] and s[j & 15] of a
-  // group are 4 consecutive words (256 and 16 are multiples of 4), read as
-  // one 16-byte vector each; the 4 outputs are one 16-byte store. E is a
-  // multiple of 4, so e0 = team*E + j0 is too and e0 + i = e0 | i.
+  // The innermost region when E is a multiple of 256 and n >= 64, frames in
+  // the slab. Summed over the levels, arr[j & 255] ^ s[j & 15] depends on
+  // j & 255 alone (16 divides 256), so thread tid takes the groups of 4
+  // elements of one class q = tid mod 64 (j0 & 255 = 4q): it sums the
+  // class's 4 words over the levels once, then writes j0 = 4q + 256p for
+  // its periods p = tid / 64, + P, + 2P, ... < E / 256, P being the number
+  // of the region's threads in class q. Every element is written by one
+  // thread, and a warp's 32 threads write 512 consecutive bytes.
   template <uint32_t kD>
-  __device__ static void inner4(uint32_t base, uint32_t *o, uint32_t ebase, uint32_t tid,
-                                uint32_t n, uint32_t G) {
-    const uint8_t *fs = dsr_smem + base;  // level 0's scalars; its array 64 bytes on
-    for (uint32_t g = tid; g < G; g += n) {
-      const uint32_t j0 = g << 2;
-      const uint32_t oa = 64u + 4u * (j0 & 255u), os = 4u * (j0 & 15u);
-      uint4 acc = make_uint4(0, 0, 0, 0);
+  __device__ static void inner_cls(uint32_t base, uint32_t *o, uint32_t ebase, uint32_t tid,
+                                   uint32_t n, uint32_t NP) {
+    const uint32_t q = tid & 63u;
+    const uint32_t P = (n - q + 63u) >> 6;  // threads t < n with t mod 64 == q
+    const uint8_t *fs = dsr_smem + base;    // level 0's scalars; its array 64 bytes on
+    const uint32_t oa = 64u + 16u * q, os = 16u * (q & 3u);
+    uint4 acc = make_uint4(0, 0, 0, 0);
 #pragma unroll
-      for (uint32_t m = 0; m < kD; ++m) {
-        const uint4 a = *reinterpret_cast<const uint4 *>(fs + m * kFrameBytes + oa);
-        const uint4 sv = *reinterpret_cast<const uint4 *>(fs + m * kFrameBytes + os);
-        acc.x += a.x ^ sv.x;
-        acc.y += a.y ^ sv.y;
-        acc.z += a.z ^ sv.z;
-        acc.w += a.w ^ sv.w;
-      }
-      const uint32_t e0 = ebase + j0;
+    for (uint32_t m = 0; m < kD; ++m) {
+      const uint4 a = *reinterpret_cast<const uint4 *>(fs + m * kFrameBytes + oa);
+      const uint4 sv = *reinterpret_cast<const uint4 *>(fs + m * kFrameBytes + os);
+      acc.x += a.x ^ sv.x;
+      acc.y += a.y ^ sv.y;
+      acc.z += a.z ^ sv.z;
+      acc.w += a.w ^ sv.w;
+    }
+    const uint32_t p0 = tid >> 6;
+    uint4 *dst = reinterpret_cast<uint4 *>(o) + q + (p0 << 6);
+    uint32_t e0 = ebase + (q << 2) + (p0 << 8);
+    for (uint32_t c = p0 < NP ? (NP - p0 + P - 1u) / P : 0u; c; --c) {
       uint4 r;
       r.x = mix32(e0 ^ acc.x);
       r.y = mix32((e0 | 1u) ^ acc.y);
       r.z = mix32((e0 | 2u) ^ acc.z);
       r.w = mix32((e0 | 3u) ^ acc.w);
-      *reinterpret_cast<uint4 *>(o + j0) = r;
+      *dst = r;
+      dst += P << 6;
+      e0 += P << 8;
     }
   }
 
@@ -323,15 +332,16 @@ struct ProgNested {
     uint32_t *o = reinterpret_cast<uint32_t *>(e.out + e.d->out_offset) +
                   static_cast<uint64_t>(e.team) * E;
     const uint32_t ebase = e.team * E;
-    // Each element j is written by exactly one worker; with E a multiple of
-    // 4 and the frames in the slab, the workers take groups of 4.
-    if ((E & 3u) == 0 && (k & kSmemArg)) {
+    // Each element j is written by exactly one thread: by classes of 4 (the
+    // frames in the slab, E a multiple of 256, 64 threads or more), or one
+    // element j = tid, tid + n, ... at a time.
+    if ((E & 255u) == 0 && n >= 64u && (k & kSmemArg)) {
       const uint32_t base = k & ~kSmemArg;
       switch (D) {
-        case 1: inner4<1>(base, o, ebase, tid, n, E >> 2); return;
-        case 2: inner4<2>(base, o, ebase, tid, n, E >> 2); return;
-        case 3: inner4<3>(base, o, ebase, tid, n, E >> 2); return;
-        default: inner4<4>(base, o, ebase, tid, n, E >> 2); return;
+        case 1: inner_cls<1>(base, o, ebase, tid, n, E >> 8); return;
+        case 2: inner_cls<2>(base, o, ebase, tid, n, E >> 8); return;
+        case 3: inner_cls<3>(base, o, ebase, tid, n, E >> 8); return;
+        default: inner_cls<4>(base, o, ebase, tid, n, E >> 8); return;
       }
     }
     for (uint32_t j = tid; j < E; j += n) {

@@ -110,7 +110,10 @@ def test_nested_smem_overflow_equivalence(rt, slab, spill):
 
 @pytest.mark.parametrize("teams,threads,depth,E,width", [
     (1, 64, 1, 7, 0), (3, 1024, 4, 5000, 0), (9, 96, 2, 333, 0), (4, 256, 3, 4096, 100),
-    (2, 32, 3, 64, 0)])
+    (2, 32, 3, 64, 0),
+    # the innermost region by classes of j & 255: n = 64 exactly, n not a
+    # multiple of 64, more threads than periods (some threads write nothing)
+    (2, 96, 1, 256, 64), (5, 128, 2, 1280, 0), (3, 1024, 3, 2048, 0), (2, 1024, 4, 256, 0)])
 def test_nested_shapes(rt, teams, threads, depth, E, width):
     work = wl.nested(teams=teams, threads=threads, depth=depth, elems_per_team=E)
     work.regions[0].width = width

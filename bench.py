@@ -71,7 +71,7 @@ SERVE_SHAPES = [dict(threads=256, slab_bytes=16384), dict(threads=128, slab_byte
 # (profiles/nested_1024x256_d3_traffic.md), keyed by a hash of the code of
 # the sources that kernel is built from (comments and white space left
 # out); any change to that code makes it null.
-TRAFFIC_BY_SOURCE = {}
+TRAFFIC_BY_SOURCE = {"c794b5bfcdd080c8": 18203341}
 KERNEL_SOURCES = ["include/dsr_runtime.cuh", "include/dsr_check.cuh", "include/dsr_kernels.cuh",
                   "include/dsr.h", "paper_1711_10413_gb300/csrc/dsr_programs.cuh",
                   "paper_1711_10413_gb300/csrc/dsr_capi.cu"]
@@ -487,8 +487,14 @@ def measure_workers(dsr, torch, device, flush, sm_count):
 
 
 def measure_forms(dsr, torch, device, flush, hbm_gbs, which=FORMS, instances=10000,
-                  sweep_sizes=None, tuning=None):
+                  sweep_sizes=None, tuning=None, dist=None):
+    """The other launch forms. With several ranks (torchrun) only the batched
+    and served forms run, each rank on its share of the instances or
+    requests with no data-path collective; the single-instance workloads
+    (sweep, scalars, workers) are measured on one GPU."""
     forms = {}
+    if dist is not None:
+        which = [f for f in which if f in ("batched", "served")]
     sm_count = torch.cuda.get_device_properties(device).multi_processor_count
     peak = smem_peak(dsr, torch, device, sm_count)
     forms["smem_peak"] = dict(gbs=peak["gbs"], source=peak["source"],
@@ -499,9 +505,9 @@ def measure_forms(dsr, torch, device, flush, hbm_gbs, which=FORMS, instances=100
     if "scalars" in which:
         forms.update(measure_scalars(dsr, torch, rt, flush))
     if "batched" in which:
-        forms.update(measure_batched(dsr, torch, rt, flush, sm_count, instances, tuning))
+        forms.update(measure_batched(dsr, torch, rt, flush, sm_count, instances, tuning, dist))
     if "served" in which:
-        forms.update(measure_served(dsr, rt))
+        forms.update(measure_served(dsr, rt, dist))
     rt.close()
     if "workers" in which:
         forms["workers"] = measure_workers(dsr, torch, device, flush, sm_count)
@@ -529,47 +535,93 @@ def measure_scalars(dsr, torch, rt, flush):
     return forms
 
 
-def measure_batched(dsr, torch, rt, flush, sm_count, instances=10000, tuning=None):
+def batch_share(instances: int, rank: int, world: int):
+    """This rank's instances of the batched form: the contiguous range of the
+    `instances`-instance hetero draw that balanced_ranges gives it by team
+    count (all of them on one GPU)."""
+    from paper_1711_10413_gb300 import shard
+    teams = wl.hetero_shapes(instances)[0]
+    a, b = shard.balanced_ranges(teams, world)[rank]
+    return np.arange(a, b)
+
+
+def served_share(descs_teams, rank: int, world: int):
+    """The requests this rank serves, by least outstanding teams
+    (route_requests), in arrival order."""
+    from paper_1711_10413_gb300 import shard
+    return np.nonzero(shard.route_requests(descs_teams, world) == rank)[0]
+
+
+def _pool_latencies(lat, dist):
+    """Every rank's latencies, on rank 0 (None elsewhere)."""
+    if dist is None:
+        return lat
+    parts = [None] * dist.get_world_size() if dist.get_rank() == 0 else None
+    dist.gather_object(lat, parts, dst=0)
+    return np.concatenate(parts) if parts is not None else None
+
+
+def measure_batched(dsr, torch, rt, flush, sm_count, instances=10000, tuning=None, dist=None):
+    """The batched form on this rank's share of the instances (all of them on
+    one GPU); with several ranks every figure is the job's: instances of all
+    ranks over the slowest rank's time."""
+    from paper_1711_10413_gb300 import shard
     forms = {}
-    # hetero instances: batched vs per-launch
+    world = dist.get_world_size() if dist else 1
+    rank = dist.get_rank() if dist else 0
+    mine = batch_share(instances, rank, world)
     rt.configure(16384, 3 * 32768, 4096)
-    work = wl.hetero(n_instances=instances)
+    work = wl.hetero(n_instances=instances, instances=mine)
     b = rt.batch_buffers(work)
     if tuning is None:
         tuning, _ = rt.autotune(b)
-    ms_batch = _event_ms(torch, lambda: rt.launch_batch(b, tuning, use_graph=True), 5, flush)
+    if dist:
+        dist.barrier()
+    ms_batch = shard.max_over_ranks(
+        _event_ms(torch, lambda: rt.launch_batch(b, tuning, use_graph=True), 5, flush), dist)
     err, counted = rt.batch_errors(b)
-    ms_plain = _event_ms(torch, lambda: rt.launch_regions(b), 2, flush)
+    ms_plain = shard.max_over_ranks(_event_ms(torch, lambda: rt.launch_regions(b), 2, flush), dist)
     st = b["status"].cpu().numpy().view(dsr.TEAM_STATUS_DTYPE)
     # the same per-instance launches with each launch's slab sized from its
     # region's footprint instead of one 16 KiB slab for all
     rt.configure(dsr.DSR_SLAB_AUTO, 3 * 32768, 4096)
-    ms_auto = _event_ms(torch, lambda: rt.launch_regions(b), 2, flush)
+    ms_auto = shard.max_over_ranks(_event_ms(torch, lambda: rt.launch_regions(b), 2, flush), dist)
     rt.configure(16384, 3 * 32768, 4096)
-    stack = hetero_stack_bytes(work.regions)
+    stack = shard.sum_over_ranks(hetero_stack_bytes(work.regions), dist)
+    push_pop = shard.sum_over_ranks(sum(r.teams * r.depth for r in work.regions), dist)
+    counted = int(shard.sum_over_ranks(counted, dist))
+    err = int(shard.sum_over_ranks(err, dist))
+    bad = int(shard.sum_over_ranks(int((st["status"] != 0).sum()), dist))
     smem_gbs = stack / (ms_batch * 1e-3) / 1e9
     forms["batched"] = dict(workload="hetero_%d_instances" % instances, instances=instances,
                             teams=counted, tuning=tuning,
+                            ranks=world, scaling="strong" if world > 1 else None,
                             batched_regions_per_s=instances / (ms_batch * 1e-3),
                             per_launch_regions_per_s=instances / (ms_plain * 1e-3),
                             per_launch_auto_slab_regions_per_s=instances / (ms_auto * 1e-3),
-                            batched_push_pop_per_s=sum(r.teams * r.depth for r in work.regions)
-                            / (ms_batch * 1e-3),
+                            batched_push_pop_per_s=push_pop / (ms_batch * 1e-3),
                             speedup=ms_plain / ms_batch,
                             stack_roofline=dict(bound="smem", stack_bytes=stack,
                                                 achieved=smem_gbs,
-                                                peak=smem_peak_gbs(sm_count), unit="GB/s",
-                                                frac=smem_gbs / smem_peak_gbs(sm_count),
+                                                peak=world * smem_peak_gbs(sm_count),
+                                                unit="GB/s",
+                                                frac=smem_gbs / (world * smem_peak_gbs(sm_count)),
                                                 peak_source=_SMEM_PEAK.get("source", "derived"),
-                                                derived_peak=smem_derived_gbs(sm_count)),
-                            device_rejects=err,
-                            bad_team_status=int((st["status"] != 0).sum()))
+                                                derived_peak=world * smem_derived_gbs(sm_count)),
+                            device_rejects=err, bad_team_status=bad)
     del b
     return forms
 
 
-def measure_served(dsr, rt):
+def measure_served(dsr, rt, dist=None):
+    """The served form: each rank serves the requests routed to it (all of
+    them on one GPU) with its own server, at the requests' arrival times;
+    the job's latency percentiles pool every rank's requests and its
+    sustained rate is all requests over the slowest rank's span."""
+    from paper_1711_10413_gb300 import shard
     forms = {}
+    world = dist.get_world_size() if dist else 1
+    rank = dist.get_rank() if dist else 0
     # hetero requests: served at several rates vs per-request launches. 100,000
     # requests per rate cycle over 20,000 distinct instances (a request's
     # twins rewrite the same output rows with the same values); the first
@@ -588,32 +640,53 @@ def measure_served(dsr, rt):
         bs = rt.serve_start(sw, threads=shape["threads"], slab_bytes=shape["slab_bytes"],
                             capacity=8192)
         descs = np.tile(bs["descs"], n // distinct)
+        mine = served_share(descs["teams"], rank, world)
+        is_warm = mine >= warm  # requests after the first 10 % of the stream
         res = {}
         try:
             for rate in (50000, 100000, 200000, 500000):
-                lat, el = dsr.dsr_serve_bench(rt.ctx, descs, wl.poisson_arrivals(n, float(rate)))
-                ok = lat[warm:][lat[warm:] >= 0]
-                res[str(rate)] = dict(p50_us=float(np.percentile(ok, 50)) / 1e3,
-                                      p99_us=float(np.percentile(ok, 99)) / 1e3,
-                                      sustained_regions_per_s=n / (el * 1e-9),
-                                      failed=int((lat < 0).sum()))
+                arrivals = wl.poisson_arrivals(n, float(rate))[mine]
+                if dist:
+                    dist.barrier()
+                lat, el = dsr.dsr_serve_bench(rt.ctx, descs[mine], arrivals)
+                el = shard.max_over_ranks(el, dist)
+                failed = int(shard.sum_over_ranks(int((lat < 0).sum()), dist))
+                pooled = _pool_latencies(lat[is_warm], dist)
+                if rank == 0:
+                    ok = pooled[pooled >= 0]
+                    res[str(rate)] = dict(p50_us=float(np.percentile(ok, 50)) / 1e3,
+                                          p99_us=float(np.percentile(ok, 99)) / 1e3,
+                                          sustained_regions_per_s=n / (el * 1e-9),
+                                          failed=failed)
             # closed loop: every request due at once, so the ring stays full
             # and the server runs at its own capacity
-            lat, el = dsr.dsr_serve_bench(rt.ctx, descs, np.zeros(n, dtype=np.int64))
-            res["capacity"] = dict(regions_per_s=n / (el * 1e-9), failed=int((lat < 0).sum()))
+            if dist:
+                dist.barrier()
+            lat, el = dsr.dsr_serve_bench(rt.ctx, descs[mine], np.zeros(len(mine), dtype=np.int64))
+            el = shard.max_over_ranks(el, dist)
+            failed = int(shard.sum_over_ranks(int((lat < 0).sum()), dist))
+            res["capacity"] = dict(regions_per_s=n / (el * 1e-9), failed=failed)
         finally:
             rt.serve_stop()
         served["%d_threads_%d_slab" % (shape["threads"], shape["slab_bytes"])] = res
     launched = {}
     for rate in (50000, 100000):
         m = 5000
-        lat, el = dsr.dsr_launch_bench(rt.ctx, bs["descs"][:m], wl.poisson_arrivals(m, float(rate)),
+        sel = served_share(bs["descs"]["teams"][:m], rank, world)
+        if dist:
+            dist.barrier()
+        lat, el = dsr.dsr_launch_bench(rt.ctx, bs["descs"][:m][sel],
+                                       wl.poisson_arrivals(m, float(rate))[sel],
                                        bs["images"], bs["out"], bs["status"])
-        launched[str(rate)] = dict(p50_us=float(np.percentile(lat, 50)) / 1e3,
-                                   p99_us=float(np.percentile(lat, 99)) / 1e3,
-                                   sustained_regions_per_s=m / (el * 1e-9))
+        el = shard.max_over_ranks(el, dist)
+        pooled = _pool_latencies(lat, dist)
+        if rank == 0:
+            launched[str(rate)] = dict(p50_us=float(np.percentile(pooled, 50)) / 1e3,
+                                       p99_us=float(np.percentile(pooled, 99)) / 1e3,
+                                       sustained_regions_per_s=m / (el * 1e-9))
     forms["served"] = dict(workload="hetero_poisson_%d_requests_%d_distinct" % (n, distinct),
-                           warmup_dropped=warm, overflow_pool_bytes=pool_per_cta * pool_ctas,
+                           ranks=world, warmup_dropped=warm,
+                           overflow_pool_bytes=pool_per_cta * pool_ctas,
                            server=served, per_request_launch=launched)
     return forms
 
@@ -819,12 +892,26 @@ def main():
     torch.cuda.synchronize()
     e2e_serial_s = shard.max_over_ranks((time.perf_counter() - t1) / args.steps, dist)
 
+    # the other launch forms (every rank takes part: with several ranks the
+    # batched and served forms run on each rank's share)
+    peaks = _peaks()
+    which = FORMS if args.forms == "all" else [f for f in args.forms.split(",")
+                                               if f and f != "none"]
+    forms = None
+    if which:
+        sizes = [int(x) for x in args.sweep_sizes.split(",") if x]
+        tuning = None
+        if args.tuning:
+            th, sl = (int(x) for x in args.tuning.split(","))
+            tuning = dict(threads=th, slab_bytes=sl, ctas_per_sm=0)
+        forms = measure_forms(dsr, torch, local, flush, peaks["hbm_gbs"], which,
+                              args.instances, sizes or None, tuning, dist)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
 
-    peaks = _peaks()
     regions_per_s = regions_done * 1000.0 / ms_step
     achieved = algo_bytes / (ms_step * 1e-3) / 1e9
     line = dict(
@@ -853,16 +940,8 @@ def main():
         smem_footprint=smem_footprint(torch, rt, region, local),
         clocks=clk,
     )
-    which = FORMS if args.forms == "all" else [f for f in args.forms.split(",")
-                                               if f and f != "none"]
-    if world == 1 and which:
-        sizes = [int(x) for x in args.sweep_sizes.split(",") if x]
-        tuning = None
-        if args.tuning:
-            th, sl = (int(x) for x in args.tuning.split(","))
-            tuning = dict(threads=th, slab_bytes=sl, ctas_per_sm=0)
-        line["forms"] = measure_forms(dsr, torch, local, flush, peaks["hbm_gbs"], which,
-                                      args.instances, sizes or None, tuning)
+    if forms is not None:
+        line["forms"] = forms
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(work, slab, ovf, args.cpu_budget)
     print(json.dumps(line))

@@ -250,12 +250,14 @@ __global__ void __launch_bounds__(MAXT, MINB) batch_kernel(const __grid_constant
 
 using BatchFn = void (*)(dsr_batch_plan);
 
-// Three register budgets: small CTAs held to 32 registers so that many of
-// them (many tasks in flight) fit an SM; the others up to 64.
+// Register budgets: CTAs of up to 512 threads are held to 32 registers, so
+// that 2048 threads (many teams in flight, or wide teams with many workers)
+// fit an SM; 1024-thread CTAs get up to 64.
 template <class P>
 BatchFn pick_batch(uint32_t threads) {
   if (threads <= 128) return batch_kernel<P, 128, 16>;
-  if (threads <= 256) return batch_kernel<P, 256, 4>;
+  if (threads <= 256) return batch_kernel<P, 256, 8>;
+  if (threads <= 512) return batch_kernel<P, 512, 4>;
   return batch_kernel<P, 1024, 1>;
 }
 

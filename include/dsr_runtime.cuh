@@ -39,6 +39,7 @@ namespace dsr {
 
 constexpr uint32_t kForkBar = 1;
 constexpr uint32_t kJoinBar = 2;
+constexpr uint32_t kWorkerBar = 3;  // the workers alone, inside a region the runtime runs
 constexpr uint32_t kTerminate = 0xFFFFFFFFu;
 constexpr uint32_t kCopyWork = 0xFFFFFFF0u;  // runtime-internal: workers copy a frame image
 constexpr uint32_t kCtrlBytes = 384;  // control block, slab starts after it
@@ -84,6 +85,7 @@ struct __align__(16) Ctrl {
   uint8_t *wovf;         // warp 0's overflow share
   uint64_t wovf_bytes;   // overflow bytes per warp (a multiple of 16)
   uint32_t wfail;        // a worker frame fitted neither share
+  uint32_t copy_x0;      // kCopyWork: XOR of word 0 on top of copy_key
 };
 static_assert(sizeof(Ctrl) <= kCtrlBytes, "control block too large");
 
@@ -405,15 +407,17 @@ __device__ __forceinline__ void copy_xor(uint8_t *dst, const uint8_t *src, uint3
   for (uint32_t w = w0 + idx; w < bytes / 4u; w += nthr) dw[w] = __ldg(sw + w) ^ key;
 }
 
-// Fill a frame from a global image, word by word XOR `key` (master warp).
-// Shared-memory frames with 16-byte aligned source and size take one bulk
-// copy issued by the master (a single thread moves the whole frame) and are
-// then keyed in place; other frames are copied by the 32 lanes, with 16-byte
-// vector accesses where alignment allows (kWide) or word by word (the
-// register-lean form used by kernels held to 32 registers).
+// Fill a frame from a global image, word by word XOR `key`, word 0 also XOR
+// `x0` (master warp). Shared-memory frames with 16-byte aligned source and
+// size take one bulk copy issued by the master (a single thread moves the
+// whole frame) and are then keyed in place; other frames are copied by the
+// 32 lanes, with 16-byte vector accesses where alignment allows (kWide) or
+// word by word (the register-lean form used by kernels held to 32
+// registers), or by the workers when large. Word 0 is XORed by the thread
+// that copies it, so a frame in global memory takes no extra round trip.
 template <bool kWide>
 __device__ __forceinline__ void fill(Stack &s, uint8_t *dst, bool dst_smem, const uint8_t *src,
-                                     uint32_t bytes, uint32_t key) {
+                                     uint32_t bytes, uint32_t key, uint32_t x0 = 0) {
   const uint32_t lane = lane_id();
   const bool aligned = ((reinterpret_cast<uintptr_t>(src) | bytes) & 15u) == 0;
   if (dst_smem && aligned && bytes >= 64) {
@@ -437,11 +441,11 @@ __device__ __forceinline__ void fill(Stack &s, uint8_t *dst, bool dst_smem, cons
       set_status(s, DSR_ERR_TIMEOUT);
     }
     s.bits ^= 0x100u;
-    if (key != 0) {
+    if (key != 0 || x0 != 0) {
       uint4 *v = reinterpret_cast<uint4 *>(dst);
       for (uint32_t i = lane; i < bytes / 16u; i += 32u) {
         uint4 x = v[i];
-        x.x ^= key;
+        x.x ^= key ^ (i == 0 ? x0 : 0u);
         x.y ^= key;
         x.z ^= key;
         x.w ^= key;
@@ -458,6 +462,7 @@ __device__ __forceinline__ void fill(Stack &s, uint8_t *dst, bool dst_smem, cons
       c->copy_dst = dst;
       c->copy_bytes = bytes;
       c->copy_key = key;
+      c->copy_x0 = x0;
     }
     named_arrive(kForkBar, team_threads());
     named_bar(kJoinBar, team_threads());
@@ -467,14 +472,14 @@ __device__ __forceinline__ void fill(Stack &s, uint8_t *dst, bool dst_smem, cons
     const uint4 *sv = reinterpret_cast<const uint4 *>(src);
     uint4 *dv = reinterpret_cast<uint4 *>(dst);
     for (uint32_t i = lane; i < nv; i += 64u) {
-      uint4 x0 = __ldg(sv + i), x1 = make_uint4(0, 0, 0, 0);
+      uint4 y0 = __ldg(sv + i), x1 = make_uint4(0, 0, 0, 0);
       const bool two = i + 32u < nv;
       if (two) x1 = __ldg(sv + i + 32u);
-      x0.x ^= key;
-      x0.y ^= key;
-      x0.z ^= key;
-      x0.w ^= key;
-      dv[i] = x0;
+      y0.x ^= key ^ (i == 0 ? x0 : 0u);
+      y0.y ^= key;
+      y0.z ^= key;
+      y0.w ^= key;
+      dv[i] = y0;
       if (two) {
         x1.x ^= key;
         x1.y ^= key;
@@ -485,11 +490,13 @@ __device__ __forceinline__ void fill(Stack &s, uint8_t *dst, bool dst_smem, cons
     }
     const uint32_t *sw = reinterpret_cast<const uint32_t *>(src);
     uint32_t *dw = reinterpret_cast<uint32_t *>(dst);
-    for (uint32_t w = nv * 4u + lane; w < bytes / 4u; w += 32u) dw[w] = __ldg(sw + w) ^ key;
+    for (uint32_t w = nv * 4u + lane; w < bytes / 4u; w += 32u)
+      dw[w] = __ldg(sw + w) ^ key ^ (w == 0 ? x0 : 0u);
   } else {
     const uint32_t *sw = reinterpret_cast<const uint32_t *>(src);
     uint32_t *dw = reinterpret_cast<uint32_t *>(dst);
-    for (uint32_t w = lane; w < bytes / 4u; w += 32u) dw[w] = __ldg(sw + w) ^ key;
+    for (uint32_t w = lane; w < bytes / 4u; w += 32u)
+      dw[w] = __ldg(sw + w) ^ key ^ (w == 0 ? x0 : 0u);
   }
   __syncwarp();
 }
@@ -678,6 +685,10 @@ __device__ __forceinline__ void worker_loop(const Env &e0) {
     if (work == kCopyWork) {
       copy_xor<P::kDense ? 1u : kBatched ? 4u : 8u>(c->copy_dst, c->copy_src, c->copy_bytes,
                                                    c->copy_key, threadIdx.x, W);
+      // worker 0 copied word 0 (the first vector, or the first word): its
+      // extra XOR, read back from the thread's own store
+      if (threadIdx.x == 0 && c->copy_x0)
+        reinterpret_cast<uint32_t *>(c->copy_dst)[0] ^= c->copy_x0;
       named_arrive(kJoinBar, team_threads());
       continue;
     }

@@ -169,7 +169,7 @@ static int32_t set_batch_attrs(dsr_ctx *ctx) {
   dsr_batch_state *b = batch_state(ctx);
   if (b->attrs_set) return DSR_OK;
   for (uint32_t p = DSR_PROG_PAPER_SCALARS; p <= DSR_PROG_HETERO; ++p)
-    for (uint32_t t : {128u, 256u, 1024u}) {
+    for (uint32_t t : {128u, 256u, 512u, 1024u}) {
       const void *k = reinterpret_cast<const void *>(batch_kernel_for(p, t));
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            ctx->max_smem_optin);

@@ -467,26 +467,143 @@ struct ProgHetero {
       if (!f) return;
       const uint32_t key = mix32(d.salt + e.team * 8u + k);
       if (staged && k == 1) wait_staged(s);
-      if (staged && f == expect)
+      if (staged && f == expect) {
         key_in_place(f, S, key);
-      else
-        fill<!kDense>(s, f, sm, img, S, key);
+        if (lane_id() == 0 && k > 1) reinterpret_cast<uint32_t *>(f)[0] ^= c_prev;
+      } else {
+        // F_k[0] ^= c_{k-1} applied by the thread that copies word 0
+        fill<!kDense>(s, f, sm, img, S, key, k > 1 ? c_prev : 0u);
+      }
       expect += (S + 15u) & ~15u;
       if (s.status() != DSR_OK) return;
       img += (S + 15u) & ~15u;
       if (lane_id() == 0) {
-        if (k > 1) reinterpret_cast<uint32_t *>(f)[0] ^= c_prev;
-        if (k < D) ctrl()->acc = 0;  // the update region's workers sum F_k here
+        // the update region's workers sum F_k here; the innermost region
+        // gets the shared-memory offset of its accumulator (0: none)
+        const uint32_t need = 4u * width;
+        ctrl()->acc = k < D ? 0u
+                      : (width >= 4u && s.sp + need <= s.slab_bytes ? kCtrlBytes + s.sp : 0u);
       }
       __syncwarp();
-      parallel<ProgHetero>(e, k < D ? kUpdate : kInner, width, k);
-      if (k < D) {
-        c_prev = ctrl()->acc;
-        set_chk(s, k - 1, c_prev);
+      if (k == D) {
+        // F_D[0], the last check word, is final now (the innermost region
+        // only reads the frames): loaded before the fork, used after the join
+        c_prev = reinterpret_cast<const uint32_t *>(f)[0];
       }
+      parallel<ProgHetero>(e, k < D ? kUpdate : kInner, width, k);
+      if (k < D) c_prev = ctrl()->acc;
+      set_chk(s, k - 1, c_prev);
     }
-    set_chk(s, D - 1, frame_words(D - 1)[0]);
     for (uint32_t k = D; k >= 1; --k) pop(s, ctrl()->frames[k - 1].ptr, d.frame_bytes[k - 1]);
+  }
+
+  // A thread's words w = v, v + n, ... < L of a frame: the sum of
+  // mix32(F[w] ^ tag ^ w), in rounds of four and then two with the round's
+  // loads issued before any of its hashing (a spilled frame's words are L2
+  // round trips). Wrap-around sums: any order gives the same value.
+  __device__ static uint32_t hash_words(const uint32_t *f, uint32_t v, uint32_t L, uint32_t n,
+                                        uint32_t tag) {
+    uint32_t acc = 0, w = v;
+    for (; w + 3u * n < L; w += 4u * n) {
+      const uint32_t x0 = f[w], x1 = f[w + n], x2 = f[w + 2u * n], x3 = f[w + 3u * n];
+      acc += (mix32(x0 ^ tag ^ w) + mix32(x1 ^ tag ^ (w + n))) +
+             (mix32(x2 ^ tag ^ (w + 2u * n)) + mix32(x3 ^ tag ^ (w + 3u * n)));
+    }
+    if (w + n < L) {
+      const uint32_t x0 = f[w], x1 = f[w + n];
+      acc += mix32(x0 ^ tag ^ w) + mix32(x1 ^ tag ^ (w + n));
+      w += 2u * n;
+    }
+    if (w < L) acc += mix32(f[w] ^ tag ^ w);
+    return acc;
+  }
+
+  // Update region: F[w] = mix32(F[w] + w) for every word, and the sum of
+  // the new words. Each word's update stands alone, so the workers take the
+  // frame by 16-byte vectors (vector i by worker i mod W, two vectors in
+  // flight per round) instead of thread by thread: every word is updated
+  // once, as the region's threads would, with many words in flight.
+  __device__ static uint32_t update_frame(uint32_t *f, uint32_t L, uint32_t first, uint32_t W) {
+    uint4 *f4 = reinterpret_cast<uint4 *>(f);  // frames are 16-byte aligned
+    const uint32_t nv = L / 4u;
+    uint32_t part = 0, i = first;
+    for (; i + W < nv; i += 2u * W) {
+      uint4 a = f4[i], b = f4[i + W];
+      const uint32_t wa = 4u * i, wb = 4u * (i + W);
+      a.x = mix32(a.x + wa);
+      a.y = mix32(a.y + wa + 1u);
+      a.z = mix32(a.z + wa + 2u);
+      a.w = mix32(a.w + wa + 3u);
+      b.x = mix32(b.x + wb);
+      b.y = mix32(b.y + wb + 1u);
+      b.z = mix32(b.z + wb + 2u);
+      b.w = mix32(b.w + wb + 3u);
+      f4[i] = a;
+      f4[i + W] = b;
+      part += (a.x + a.y) + (a.z + a.w) + (b.x + b.y) + (b.z + b.w);
+    }
+    if (i < nv) {
+      uint4 a = f4[i];
+      const uint32_t wa = 4u * i;
+      a.x = mix32(a.x + wa);
+      a.y = mix32(a.y + wa + 1u);
+      a.z = mix32(a.z + wa + 2u);
+      a.w = mix32(a.w + wa + 3u);
+      f4[i] = a;
+      part += (a.x + a.y) + (a.z + a.w);
+    }
+    for (uint32_t w = 4u * nv + first; w < L; w += W) {  // the last L mod 4 words
+      const uint32_t y = mix32(f[w] + w);
+      f[w] = y;
+      part += y;
+    }
+    return part;
+  }
+
+  // Innermost region with a shared-memory accumulator of n words at byte
+  // `acc_off`: out[v] = sum over the frames m and their words w with
+  // w mod n == v of mix32(F_m[w] ^ (m+1) << 24 ^ w). The workers take each
+  // frame by 16-byte vectors (vector i by worker i mod W) and add each word's
+  // hash into acc[w mod n] with a shared-memory atomic; two barriers of the
+  // workers alone (named barrier 3) separate clearing, adding and writing
+  // out. Wrap-around adds: the same sums as each thread's own loop.
+  // acc[(w + c) mod n] += mix32(x.c ^ tag ^ (w + c)) for the 4 words of a
+  // vector starting at word w, r = w mod n.
+  __device__ static void add_vec(uint32_t *acc, const uint4 x, uint32_t w, uint32_t tag,
+                                 uint32_t r, uint32_t n) {
+    uint32_t r1 = r + 1u, r2 = r + 2u, r3 = r + 3u;
+    r1 = r1 >= n ? r1 - n : r1;
+    r2 = r2 >= n ? r2 - n : r2;
+    r3 = r3 >= n ? r3 - n : r3;
+    atomicAdd(acc + r, mix32(x.x ^ tag ^ w));
+    atomicAdd(acc + r1, mix32(x.y ^ tag ^ (w + 1u)));
+    atomicAdd(acc + r2, mix32(x.z ^ tag ^ (w + 2u)));
+    atomicAdd(acc + r3, mix32(x.w ^ tag ^ (w + 3u)));
+  }
+
+  __device__ static void inner_acc(const Env &e, uint32_t first, uint32_t W, uint32_t n,
+                                   uint32_t D, uint32_t acc_off) {
+    const Ctrl *c = ctrl();
+    uint32_t *acc = reinterpret_cast<uint32_t *>(dsr_smem + acc_off);
+    for (uint32_t v = first; v < n; v += W) acc[v] = 0u;
+    named_bar(kWorkerBar, W);
+    const uint32_t step = (4u * W) % n;  // n >= 4
+    for (uint32_t m = 0; m < D; ++m) {
+      const uint32_t *f = reinterpret_cast<const uint32_t *>(c->frames[m].ptr);
+      const uint32_t L = c->frames[m].bytes / 4u, nv = L / 4u, tag = (m + 1u) << 24;
+      const uint4 *f4 = reinterpret_cast<const uint4 *>(f);
+      uint32_t r = (4u * first) % n;  // (4 i) mod n for this worker's vector i
+      for (uint32_t i = first; i < nv; i += W) {
+        add_vec(acc, f4[i], 4u * i, tag, r, n);
+        r += step;
+        r = r >= n ? r - n : r;
+      }
+      for (uint32_t w = 4u * nv + first; w < L; w += W) atomicAdd(acc + w % n, mix32(f[w] ^ tag ^ w));
+    }
+    named_bar(kWorkerBar, W);
+    uint32_t *o = reinterpret_cast<uint32_t *>(e.out + e.d->out_offset) +
+                  static_cast<uint64_t>(e.team) * n;
+    for (uint32_t v = first; v < n; v += W) o[v] = acc[v];
   }
 
   // The worker's virtual threads with the frame pointers and sizes read
@@ -499,17 +616,14 @@ struct ProgHetero {
                              uint32_t n, uint32_t k) {
     Ctrl *c = ctrl();
     if (work == kUpdate) {
-      uint32_t *f = reinterpret_cast<uint32_t *>(c->frames[k - 1].ptr);
-      const uint32_t L = c->frames[k - 1].bytes / 4u;
-      uint32_t part = 0;
-      for (uint32_t v = first; v < n && v < L; v += W)
-        for (uint32_t w = v; w < L; w += n) {
-          const uint32_t x = mix32(f[w] + w);
-          f[w] = x;
-          part += x;
-        }
+      uint32_t part = update_frame(reinterpret_cast<uint32_t *>(c->frames[k - 1].ptr),
+                                   c->frames[k - 1].bytes / 4u, first, W);
       part = warp_sum(part);
       if (lane_id() == 0 && part) atomicAdd(&c->acc, part);
+      return;
+    }
+    if (const uint32_t acc_off = c->acc) {
+      inner_acc(e, first, W, n, k, acc_off);
       return;
     }
     const uint32_t *f[DSR_MAX_DEPTH];
@@ -527,12 +641,8 @@ struct ProgHetero {
     for (; v < n && v < Lmax; v += W) {
       uint32_t acc = 0;
 #pragma unroll
-      for (uint32_t m = 0; m < DSR_MAX_DEPTH; ++m) {
-        if (m < k) {
-          const uint32_t tag = (m + 1u) << 24;
-          for (uint32_t w = v; w < L[m]; w += n) acc += mix32(f[m][w] ^ tag ^ w);
-        }
-      }
+      for (uint32_t m = 0; m < DSR_MAX_DEPTH; ++m)
+        if (m < k) acc += hash_words(f[m], v, L[m], n, (m + 1u) << 24);
       o[v] = acc;
     }
     for (; v < n; v += W) o[v] = 0u;

@@ -455,8 +455,9 @@ typedef struct dsr_batch_plan {
  * expansion of the (instance, team) task list into the workspace, and fills
  * *plan with the persistent kernel's grid and arguments. The caller then
  * launches the kernel on the same stream with dynamic shared memory
- * plan->slab_bytes + DSR control block (the launch template of
- * dsr_device.cuh does both). Errors: as dsr_launch_batch. */
+ * plan->slab_bytes plus the control block and the accumulator area
+ * (dsr::batch_smem; the launch template of dsr_device.cuh does both).
+ * Errors: as dsr_launch_batch. */
 int32_t dsr_batch_prepare(dsr_ctx *ctx, const dsr_region_desc *descs_dev, uint32_t n,
                           uint32_t program, uint64_t total_teams, const void *images_dev,
                           uint64_t image_bytes, void *out_dev, uint64_t out_bytes,

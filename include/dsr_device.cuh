@@ -331,7 +331,7 @@ int32_t dsr_launch_user_batch(dsr_ctx *ctx, const dsr_region_desc *descs_dev, ui
   // the shape is out of range: dsr_batch_prepare then says why)
   uint32_t per_sm = 0;
   const dsr::BatchFn k = dsr::pick_batch<P>(t.threads);
-  const uint32_t smem = dsr::kCtrlBytes + t.slab_bytes;
+  const uint32_t smem = dsr::batch_smem(t.slab_bytes);
   int device = 0;
   if (t.threads >= 64 && t.threads <= DSR_MAX_THREADS && t.threads % 32 == 0 &&
       t.slab_bytes % 16 == 0 && cudaGetDevice(&device) == cudaSuccess &&
@@ -351,7 +351,7 @@ int32_t dsr_launch_user_batch(dsr_ctx *ctx, const dsr_region_desc *descs_dev, ui
                                  workspace_dev, workspace_bytes, t.threads, t.slab_bytes, per_sm,
                                  stream, &plan);
   if (rc != DSR_OK) return rc;
-  k<<<plan.grid, plan.threads, dsr::kCtrlBytes + plan.slab_bytes,
+  k<<<plan.grid, plan.threads, dsr::batch_smem(plan.slab_bytes),
       static_cast<cudaStream_t>(stream)>>>(plan);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return dsr_report_error(ctx, DSR_ERR_CUDA, cudaGetErrorString(e));

@@ -137,6 +137,10 @@ struct WsHeader {
 };
 static_assert(sizeof(WsHeader) == 128 + 8 * kBuckets + 128 * kGroups, "workspace header");
 
+// Dynamic shared memory of a persistent-kernel CTA with a slab of `slab`
+// bytes: control block, slab, accumulator area.
+constexpr uint32_t batch_smem(uint32_t slab) { return kCtrlBytes + slab + kAccBytes; }
+
 // The persistent kernel's master warp pulls tasks in chunks of kGrab
 // consecutive tasks (consecutive teams of one instance share its descriptor
 // and images, which then hit in cache).
@@ -225,6 +229,7 @@ __global__ void __launch_bounds__(MAXT, MINB) batch_kernel(const __grid_constant
     e.d = &c->desc;
     e.team = task.y;
     team_setup(s, a.slab_bytes, ovf, a.ovf_per_cta, a.timeout_ns, first);
+    if (first) s.bits |= kAccArea;
     first = false;
     if (!cached_ok || task.y >= c->desc.teams) {
       if (lane == 0) {

@@ -46,6 +46,11 @@ constexpr uint32_t kCtrlBytes = 384;  // control block, slab starts after it
 constexpr uint32_t kParallelCopyBytes = 2048;  // frames filled by the workers from this size
 constexpr uint32_t kStreamChunks = 8;          // mbarriers of a streamed fill
 constexpr uint32_t kStreamMinBytes = 16384;    // slab frames streamed from this size
+// The persistent kernels (batched, served) give every CTA, after its slab, a
+// region-wide accumulator of one word per thread a region may have
+// (programs whose regions reduce into per-thread sums use it).
+constexpr uint32_t kAccBytes = 4u * DSR_MAX_THREADS;
+constexpr uint32_t kAccArea = 1u << 25;  // Stack::bits: this CTA has that area
 
 struct FrameEnt {
   uint8_t *ptr;      // generic address of the frame (shared or global)
@@ -223,6 +228,7 @@ struct Stack {
                         // (bit 10) | streamed fill pending (bit 11) | live
                         // depth (bits 12-15) | frame k in the slab (bit 16 + k)
                         // | streamed-fill mbarriers initialised (bit 24)
+                        // | accumulator area after the slab (bit 25)
 
   __device__ __forceinline__ int32_t status() const { return static_cast<int32_t>(bits & 0xffu); }
   __device__ __forceinline__ uint32_t phase() const { return (bits >> 8) & 1u; }
@@ -258,8 +264,9 @@ __device__ __forceinline__ void team_setup(Stack &s, uint32_t slab_bytes, uint8_
     }
   }
   // the mbarriers' parities (fill: bit 8, streamed fill: bit 10) and the
-  // streamed fill's set-up flag (bit 24) carry over
-  s.bits = first ? 0u : (s.bits & 0x1000500u);
+  // streamed fill's set-up flag (bit 24) and the accumulator area (bit 25)
+  // carry over
+  s.bits = first ? 0u : (s.bits & 0x3000500u);
   s.slab_bytes = slab_bytes;
   s.sp = 0;
   s.gsp = 0;
@@ -740,6 +747,11 @@ __device__ __forceinline__ void team_report(const Env &e, Stack &s, dsr_team_sta
     for (int k = 0; k < DSR_MAX_DEPTH; ++k) r.chk[k] = status == DSR_OK ? chk[k] : 0u;
     st[e.d->status_index + e.team] = r;
   }
+}
+
+// Shared-memory offset of the CTA's accumulator area (0: none).
+__device__ __forceinline__ uint32_t acc_area(const Stack &s) {
+  return (s.bits & kAccArea) ? kCtrlBytes + s.slab_bytes : 0u;
 }
 
 __device__ __forceinline__ uint32_t region_width(const dsr_region_desc &d) {

@@ -227,8 +227,7 @@ int32_t check_tuning(dsr_ctx *ctx, const dsr_batch_tuning *t_in, dsr_batch_tunin
   if (t_in) *t = *t_in;
   if (t->threads < 64 || t->threads > DSR_MAX_THREADS || t->threads % 32)
     return dsr_fail(ctx, DSR_ERR_INVALID, "batch threads must be a multiple of 32 in [64, 1024]");
-  if (t->slab_bytes % 16 ||
-      kCtrlBytes + t->slab_bytes > static_cast<uint32_t>(ctx->max_smem_optin))
+  if (t->slab_bytes % 16 || batch_smem(t->slab_bytes) > static_cast<uint32_t>(ctx->max_smem_optin))
     return dsr_fail(ctx, DSR_ERR_INVALID, "batch slab must be a multiple of 16 fitting a CTA");
   return DSR_OK;
 }
@@ -242,7 +241,7 @@ int32_t builtin_per_sm(dsr_ctx *ctx, uint32_t program, const dsr_batch_tuning &t
   int occ = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       &occ, reinterpret_cast<const void *>(k), static_cast<int>(t.threads),
-      kCtrlBytes + t.slab_bytes);
+      batch_smem(t.slab_bytes));
   if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "occupancy query");
   *per_sm = t.ctas_per_sm ? std::min<uint32_t>(t.ctas_per_sm, occ) : static_cast<uint32_t>(occ);
   return DSR_OK;
@@ -292,7 +291,7 @@ int32_t enqueue_batch(dsr_ctx *ctx, const BatchCall &c, const dsr_batch_tuning &
   dsr_batch_plan a;
   int32_t rc = prepare(ctx, c, t.threads, t.slab_bytes, per_sm, s, &a);
   if (rc != DSR_OK) return rc;
-  batch_kernel_for(c.program, a.threads)<<<a.grid, a.threads, kCtrlBytes + a.slab_bytes, s>>>(a);
+  batch_kernel_for(c.program, a.threads)<<<a.grid, a.threads, batch_smem(a.slab_bytes), s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "batch launch");
   return DSR_OK;

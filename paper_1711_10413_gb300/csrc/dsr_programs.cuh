@@ -480,9 +480,11 @@ struct ProgHetero {
       if (lane_id() == 0) {
         // the update region's workers sum F_k here; the innermost region
         // gets the shared-memory offset of its accumulator (0: none)
-        const uint32_t need = 4u * width;
-        ctrl()->acc = k < D ? 0u
-                      : (width >= 4u && s.sp + need <= s.slab_bytes ? kCtrlBytes + s.sp : 0u);
+        // (the persistent kernels' area after the slab, else the slab above
+        // the frames when it has room)
+        const uint32_t need = 4u * width, area = acc_area(s);
+        ctrl()->acc = k < D || width < 4u ? 0u
+                      : area ? area : (s.sp + need <= s.slab_bytes ? kCtrlBytes + s.sp : 0u);
       }
       __syncwarp();
       if (k == D) {

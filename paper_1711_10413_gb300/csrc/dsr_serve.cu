@@ -48,6 +48,7 @@
 #include "dsr.h"
 #include "dsr_check.cuh"
 #include "dsr_ctx.h"
+#include "dsr_kernels.cuh"
 #include "dsr_programs.cuh"
 
 using namespace dsr;
@@ -365,6 +366,7 @@ __global__ void __launch_bounds__(MAXT, MINB) serve_kernel(const __grid_constant
       e.d = &c->desc;
       e.team = team;
       team_setup(s, a.slab_bytes, ovf, a.ovf_per_cta, a.timeout_ns, first);
+      if (first) s.bits |= kAccArea;
       first = false;
       int32_t st;
       if (!cached_ok) {
@@ -542,7 +544,7 @@ int32_t launch_server(dsr_ctx *ctx, dsr_serve_state *sv) {
   a.capacity = sv->cfg.capacity;
   a.slab_bytes = sv->cfg.slab_bytes;
   serve_kernel_for(sv->cfg.program, sv->cfg.threads)<<<sv->grid, sv->cfg.threads,
-                                                        kCtrlBytes + sv->cfg.slab_bytes,
+                                                        batch_smem(sv->cfg.slab_bytes),
                                                         sv->stream>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "server launch");
@@ -597,7 +599,7 @@ extern "C" int32_t dsr_serve_start(dsr_ctx *ctx, const dsr_serve_cfg *cfg, void 
   if (!serve_kernel_for(cfg->program, cfg->threads))
     return dsr_fail(ctx, DSR_ERR_INVALID, "the served form runs the scalars, nested and hetero programs");
   if (cfg->threads < 64 || cfg->threads > DSR_MAX_THREADS || cfg->threads % 32 ||
-      cfg->slab_bytes % 16 || kCtrlBytes + cfg->slab_bytes > static_cast<uint32_t>(ctx->max_smem_optin) ||
+      cfg->slab_bytes % 16 || batch_smem(cfg->slab_bytes) > static_cast<uint32_t>(ctx->max_smem_optin) ||
       cfg->capacity == 0 || cfg->capacity > (1u << 24) || !cfg->out_dev || !cfg->status_dev)
     return dsr_fail(ctx, DSR_ERR_INVALID, "bad serve configuration");
   if (!workspace_dev || (reinterpret_cast<uintptr_t>(workspace_dev) & 15u) ||
@@ -641,7 +643,7 @@ extern "C" int32_t dsr_serve_start(dsr_ctx *ctx, const dsr_serve_cfg *cfg, void 
   }
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, reinterpret_cast<const void *>(k),
-                                                cfg->threads, kCtrlBytes + cfg->slab_bytes);
+                                                cfg->threads, batch_smem(cfg->slab_bytes));
   if (occ < 1) {
     dsr_serve_release(ctx);
     return dsr_fail(ctx, DSR_ERR_INVALID, "serve CTA shape does not fit an SM");

@@ -479,13 +479,18 @@ struct dsr_serve_state {
   ServeWs *ws = nullptr;
   SlotState *slots = nullptr;
   dsr_region_desc *dring = nullptr;
-  // host bookkeeping
+  // host bookkeeping, per ring slot (ticket t uses slot t % capacity): no
+  // map on the per-request path
   uint64_t next_seq = 0;       // next ticket
   uint64_t comp_pos = 0;       // next completion record to read
   uint64_t completed = 0;      // requests completed
-  std::unordered_map<uint64_t, int32_t> done;  // ticket -> status, until polled
-  std::vector<uint8_t> slot_busy;               // slot holds an unfinished request
-  std::unordered_map<uint64_t, uint64_t> reserved;  // ticket -> overflow bytes reserved
+  std::vector<uint8_t> slot_busy;        // slot holds an unfinished request
+  std::vector<uint64_t> slot_reserved;   // its overflow bytes reserved
+  std::vector<uint64_t> slot_done;       // ticket + 1 of a completion not yet reported, or 0
+  std::vector<int32_t> slot_status;      // ... and its status
+  std::unordered_map<uint64_t, int32_t> unreported;  // completions whose slot was reused first
+  std::vector<uint64_t> just_done;       // tickets completed since the bench last looked
+  bool collect_done = false;             // a bench run is collecting them
   uint64_t reserved_bytes = 0;
   uint64_t pool_budget = 0;
   uint64_t next_alive_check = 0;  // host time of the next server-exit check
@@ -566,24 +571,39 @@ uint64_t team_spill(const dsr_region_desc &d, uint32_t slab) {
 }
 
 // Read new completion records (host side): free their slots and their
-// overflow reservations.
+// overflow reservations, and keep each status for its ticket's poll.
 void drain_completions(dsr_serve_state *sv) {
   for (;;) {
     CompRec *r = sv->comp + (sv->comp_pos % sv->cfg.capacity);
     const unsigned long long m = __atomic_load_n(&r->marker, __ATOMIC_ACQUIRE);
     if (m == 0) break;
     const uint64_t seq = m - 1;
-    sv->done[seq] = r->status;
+    const uint32_t slot = static_cast<uint32_t>(seq % sv->cfg.capacity);
+    sv->slot_done[slot] = seq + 1;
+    sv->slot_status[slot] = r->status;
     __atomic_store_n(&r->marker, 0ull, __ATOMIC_RELAXED);
     ++sv->comp_pos;
     ++sv->completed;
-    sv->slot_busy[seq % sv->cfg.capacity] = 0;
-    auto it = sv->reserved.find(seq);
-    if (it != sv->reserved.end()) {
-      sv->reserved_bytes -= it->second;
-      sv->reserved.erase(it);
-    }
+    sv->slot_busy[slot] = 0;
+    sv->reserved_bytes -= sv->slot_reserved[slot];
+    sv->slot_reserved[slot] = 0;
+    if (sv->collect_done) sv->just_done.push_back(seq);
   }
+}
+
+// Report ticket's completion once: *status, or false when it has none yet.
+bool take_done(dsr_serve_state *sv, uint64_t ticket, int32_t *status) {
+  const uint32_t slot = static_cast<uint32_t>(ticket % sv->cfg.capacity);
+  if (sv->slot_done[slot] == ticket + 1) {
+    *status = sv->slot_status[slot];
+    sv->slot_done[slot] = 0;
+    return true;
+  }
+  auto it = sv->unreported.find(ticket);
+  if (it == sv->unreported.end()) return false;
+  *status = it->second;
+  sv->unreported.erase(it);
+  return true;
 }
 
 }  // namespace
@@ -627,6 +647,9 @@ extern "C" int32_t dsr_serve_start(dsr_ctx *ctx, const dsr_serve_cfg *cfg, void 
   std::memset(sv->hs, 0, sizeof(HostShared));
   std::memset(sv->comp, 0, sizeof(CompRec) * cfg->capacity);
   sv->slot_busy.assign(cfg->capacity, 0);
+  sv->slot_reserved.assign(cfg->capacity, 0);
+  sv->slot_done.assign(cfg->capacity, 0);
+  sv->slot_status.assign(cfg->capacity, 0);
   sv->ws = static_cast<ServeWs *>(workspace_dev);
   sv->slots = reinterpret_cast<SlotState *>(static_cast<uint8_t *>(workspace_dev) + sizeof(ServeWs));
   sv->dring = reinterpret_cast<dsr_region_desc *>(sv->slots + cfg->capacity);
@@ -685,12 +708,15 @@ extern "C" int32_t dsr_serve_submit(dsr_ctx *ctx, const dsr_region_desc *d, uint
   if (sv->running && server_exited(sv)) sv->running = false;
   if (!sv->running && (rc = launch_server(ctx, sv)) != DSR_OK) return rc;
   const uint64_t seq = sv->next_seq++;
-  sv->ring[seq % sv->cfg.capacity] = *d;
-  sv->slot_busy[seq % sv->cfg.capacity] = 1;
-  if (want) {
-    sv->reserved[seq] = want;
-    sv->reserved_bytes += want;
+  const uint32_t slot = static_cast<uint32_t>(seq % sv->cfg.capacity);
+  if (sv->slot_done[slot]) {  // the slot's last completion was never polled: keep it
+    sv->unreported[sv->slot_done[slot] - 1] = sv->slot_status[slot];
+    sv->slot_done[slot] = 0;
   }
+  sv->ring[slot] = *d;
+  sv->slot_busy[slot] = 1;
+  sv->slot_reserved[slot] = want;
+  sv->reserved_bytes += want;
   __atomic_store_n(&sv->hs->tail, static_cast<unsigned long long>(seq + 1), __ATOMIC_RELEASE);
   *ticket = seq;
   return DSR_OK;
@@ -706,13 +732,7 @@ extern "C" int32_t dsr_serve_poll(dsr_ctx *ctx, uint64_t ticket, int32_t *status
     int32_t rc = launch_server(ctx, sv);
     if (rc != DSR_OK) return rc;
   }
-  auto it = sv->done.find(ticket);
-  if (it == sv->done.end()) {
-    *status = DSR_PENDING;
-    return DSR_OK;
-  }
-  *status = it->second;
-  sv->done.erase(it);
+  if (!take_done(sv, ticket, status)) *status = DSR_PENDING;
   return DSR_OK;
 }
 
@@ -763,11 +783,20 @@ extern "C" int32_t dsr_serve_bench(dsr_ctx *ctx, const dsr_region_desc *descs, u
   if (!ctx || !ctx->serve || !descs || !arrival_ns || !latency_ns)
     return dsr_fail(ctx, DSR_ERR_INVALID, "not serving or null argument");
   dsr_serve_state *sv = ctx->serve;
-  std::vector<int64_t> sched(n);
-  std::vector<uint64_t> tickets(n, ~0ull);
-  std::unordered_map<uint64_t, uint32_t> by_ticket;
+  // the request of each ring slot's ticket (a slot holds one request at a time)
+  std::vector<uint32_t> req_of_slot(sv->cfg.capacity, ~0u);
+  std::vector<uint64_t> ticket_of_slot(sv->cfg.capacity, ~0ull);
   const uint64_t t0 = now_ns() + 1000000;  // start 1 ms from now
   uint32_t next = 0, finished = 0;
+  sv->just_done.clear();
+  sv->collect_done = true;
+  struct Stop {  // stop collecting however the loop ends
+    dsr_serve_state *sv;
+    ~Stop() {
+      sv->collect_done = false;
+      sv->just_done.clear();
+    }
+  } stop_collecting{sv};
   for (uint32_t i = 0; i < n; ++i) latency_ns[i] = -1;
   const uint64_t deadline = t0 + static_cast<uint64_t>(arrival_ns[n ? n - 1 : 0]) + 30000000000ull;
   while (finished < n) {
@@ -780,22 +809,25 @@ extern "C" int32_t dsr_serve_bench(dsr_ctx *ctx, const dsr_region_desc *descs, u
       const int32_t rc = dsr_serve_submit(ctx, descs + next, &tk);
       if (rc == DSR_ERR_BUDGET) break;
       if (rc != DSR_OK) return rc;
-      tickets[next] = tk;
-      by_ticket[tk] = next;
+      req_of_slot[tk % sv->cfg.capacity] = next;
+      ticket_of_slot[tk % sv->cfg.capacity] = tk;
       ++next;
     }
     drain_completions(sv);
-    for (auto it = sv->done.begin(); it != sv->done.end();) {
-      auto f = by_ticket.find(it->first);
-      if (f == by_ticket.end()) {
-        ++it;
-        continue;
+    if (!sv->just_done.empty()) {
+      const uint64_t t_done = now_ns();
+      for (const uint64_t tk : sv->just_done) {
+        const uint32_t slot = static_cast<uint32_t>(tk % sv->cfg.capacity);
+        if (ticket_of_slot[slot] != tk) continue;  // not one of this run's requests
+        int32_t st = DSR_OK;
+        take_done(sv, tk, &st);
+        const uint32_t i = req_of_slot[slot];
+        latency_ns[i] = static_cast<int64_t>(t_done - (t0 + arrival_ns[i]));
+        if (st != DSR_OK) latency_ns[i] = -2 - st;
+        ticket_of_slot[slot] = ~0ull;
+        ++finished;
       }
-      latency_ns[f->second] = static_cast<int64_t>(now_ns() - (t0 + arrival_ns[f->second]));
-      if (it->second != DSR_OK) latency_ns[f->second] = -2 - it->second;
-      by_ticket.erase(f);
-      it = sv->done.erase(it);
-      ++finished;
+      sv->just_done.clear();
     }
   }
   if (elapsed_ns) *elapsed_ns = static_cast<int64_t>(now_ns() - t0);

@@ -193,3 +193,28 @@ def test_serve_rejects_bad_requests_on_the_host(rt):
             dsr.dsr_serve_submit(rt.ctx, other)
     finally:
         rt.serve_stop()
+
+
+@pytest.mark.parametrize("threads,slab", [(128, 8192), (256, 16384)])
+def test_serve_full_distribution_equals_oracle(rt, threads, slab):
+    """The served form on the full heterogeneous distribution (teams
+    log-uniform up to 512, threads up to 1024, frames up to 32 KiB, depth 1-3),
+    in both server shapes the bench runs: every request's output rows and
+    every team's record equal the oracle's, with up to 512 requests in flight
+    at once (frames larger than the slab go to each CTA's overflow slab)."""
+    import paper_1711_10413_gb300 as dsr
+    work = wl.hetero(n_instances=600, seed=44)
+    assert max(r.teams for r in work.regions) > 256
+    assert max(r.threads for r in work.regions) > 960
+    b = rt.serve_start(work, threads=threads, slab_bytes=slab, capacity=512)
+    try:
+        st = _wait_all(dsr, rt, _submit_all(dsr, rt, work.regions, deadline_s=60.0),
+                       deadline_s=60.0)
+    finally:
+        rt.serve_stop()
+    assert all(v == 0 for v in st.values())
+    r, rs = oracle.run_workload(work, slab_bytes=slab, overflow_bytes=3 * 32768)
+    assert np.array_equal(b["out"].cpu().numpy()[: r.size], r)
+    gs = b["status"].cpu().numpy().view(dsr.TEAM_STATUS_DTYPE)
+    for f in ("status", "depth_final", "hwm_bytes", "spill_bytes", "chk"):
+        assert np.array_equal(gs[f], rs[f]), f

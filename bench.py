@@ -458,32 +458,50 @@ def measure_workers(dsr, torch, device, flush, sm_count):
     workers pushes a 256-byte frame on its warp's stack and runs a nested
     region on its warp. Warp stacks in the slab, then all on the global
     (overflow) stack. Stack bytes per worker frame: written by the fill,
-    read and written by the nested region, read by the worker's sum."""
+    read and written by the nested region, read by the worker's sum.
+
+    Beside it, the two ways a worker's nested team (its warp's lanes) gets
+    the worker's key and frame offset, in the slab: warp shuffles (param 0)
+    against a per-warp table in shared memory (param 1), for 256-byte frames
+    (whole rows of 32 words: keys only) and 100-byte frames (the general
+    walk: keys and slot offsets at every step)."""
     teams, threads, S = 1024, 256, 256
     W = threads - 32
-    work = wl.workers(teams=teams, threads=threads, frame_bytes=S)
-    region = work.regions[0]
     rt = dsr.Runtime(device, slab_bytes=0, overflow_bytes_per_team=16 + W * S, max_teams=teams)
-    images, out, status = rt.device_buffers(work)
-    stack = teams * W * 4 * S
     runs = []
-    for where, slab, ovf in (("slab", 16 + W * S, 0), ("overflow", 16, W * S)):
+
+    def one(work, where, slab, ovf):
+        region = work.regions[0]
+        images, out, status = rt.device_buffers(work)
         rt.configure(slab, ovf, teams if ovf else 0)
         occ = rt.occupancy(region)
         ms = _event_ms(torch, lambda: dsr.dsr_launch_region(rt.ctx, region, images, out, status),
                        10, flush)
         st = status.cpu().numpy().view(dsr.TEAM_STATUS_DTYPE)
+        fb = region.frame_bytes[1]
+        stack = teams * W * 4 * ((fb + 15) // 16 * 16)
         gbs = stack / (ms * 1e-3) / 1e9
-        runs.append(dict(placement=where, us=ms * 1e3, regions_per_s=1.0 / (ms * 1e-3),
-                         worker_frames_per_s=teams * W / (ms * 1e-3), stack_bytes=stack,
-                         stack_gbs=gbs, smem_frac=gbs / smem_peak_gbs(sm_count),
-                         smem_per_team=occ["smem_per_team"], ctas_per_sm=occ["ctas_per_sm"],
-                         regs_per_thread=occ["regs_per_thread"],
-                         spill_bytes_per_team=int(st["spill_bytes"].max()),
-                         bad_team_status=int((st["status"] != 0).sum())))
+        return dict(placement=where, frame_bytes=fb, share="smem" if region.param else "shuffle",
+                    us=ms * 1e3, regions_per_s=1.0 / (ms * 1e-3),
+                    worker_frames_per_s=teams * W / (ms * 1e-3), stack_bytes=stack,
+                    stack_gbs=gbs, smem_frac=gbs / smem_peak_gbs(sm_count),
+                    smem_per_team=occ["smem_per_team"], ctas_per_sm=occ["ctas_per_sm"],
+                    regs_per_thread=occ["regs_per_thread"],
+                    spill_bytes_per_team=int(st["spill_bytes"].max()),
+                    bad_team_status=int((st["status"] != 0).sum()))
+
+    work = wl.workers(teams=teams, threads=threads, frame_bytes=S)
+    runs.append(one(work, "slab", 16 + W * S, 0))
+    runs.append(one(work, "overflow", 16, W * S))
+    sharing = []
+    for fb in (256, 100):
+        slab = 16 + W * ((fb + 15) // 16 * 16)
+        for share in (0, 1):
+            sharing.append(one(wl.workers(teams=teams, threads=threads, frame_bytes=fb,
+                                          share=share), "slab", slab, 0))
     rt.close()
     return dict(workload="workers_1024x256_256B", teams=teams, threads=threads,
-                worker_frame_bytes=S, runs=runs)
+                worker_frame_bytes=S, runs=runs, sharing_within_a_warp=sharing)
 
 
 def measure_forms(dsr, torch, device, flush, hbm_gbs, which=FORMS, instances=10000,

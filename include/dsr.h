@@ -98,7 +98,10 @@ enum {
    * out[team*width + t] = (sum G_t) ^ s2. The warp stacks share out what
    * the team's slab and overflow slab have left, evenly over the W/32
    * worker warps; a worker frame that fits neither share gives OVERFLOW.
-   * chk[0] = sum of the team's outputs. Plain launch only. */
+   * chk[0] = sum of the team's outputs. param 0: the nested teams get their
+   * workers' keys and frame offsets by warp shuffles; param 1: from a
+   * per-warp table in shared memory (the same results; the two ways of
+   * sharing within a warp, side by side). Plain launch only. */
   DSR_PROG_WORKERS = 7,
   /* First id of user-written programs: a program written against the device
    * API of dsr_device.cuh and launched through its launch templates carries

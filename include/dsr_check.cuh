@@ -56,7 +56,7 @@ DSR_HD int shape_error(const dsr_region_desc &d) {
     case DSR_PROG_HETERO:
       return 0;
     case DSR_PROG_WORKERS:
-      return (d.depth != 2 || d.frame_bytes[0] != 16 || d.threads < 64) ? 4 : 0;
+      return (d.depth != 2 || d.frame_bytes[0] != 16 || d.threads < 64 || d.param > 1) ? 4 : 0;
     default:  // a user-written program (dsr_device.cuh) states its own layout
       return d.program >= DSR_PROG_USER ? 0 : 5;
   }

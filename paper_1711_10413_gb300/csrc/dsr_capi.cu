@@ -23,7 +23,7 @@ namespace {
 
 using KernelFn = PlainFn;
 
-KernelFn plain_kernel_for(uint32_t program, uint32_t threads) {
+KernelFn plain_kernel_for(uint32_t program, uint32_t threads, uint32_t param = 0) {
   switch (program) {
     case DSR_PROG_PAPER_SCALARS: return pick_plain<ProgPaperScalars>(threads);
     case DSR_PROG_PAPER_ARRAYS: return pick_plain<ProgPaperArrays>(threads);
@@ -31,7 +31,8 @@ KernelFn plain_kernel_for(uint32_t program, uint32_t threads) {
     case DSR_PROG_NESTED: return pick_plain<ProgNested>(threads);
     case DSR_PROG_SWEEP: return pick_plain<ProgSweep>(threads);
     case DSR_PROG_HETERO: return pick_plain<ProgHetero>(threads);
-    case DSR_PROG_WORKERS: return pick_plain<ProgWorkers>(threads);
+    case DSR_PROG_WORKERS:
+      return param == 1 ? pick_plain<ProgWorkersSmem>(threads) : pick_plain<ProgWorkers>(threads);
     default: return nullptr;
   }
 }
@@ -216,11 +217,20 @@ extern "C" int32_t dsr_destroy(dsr_ctx *ctx) {
 
 static int32_t set_smem_attr(dsr_ctx *ctx, uint32_t smem) {
   static const uint32_t kThreads[] = {128, 256, 512, 1024};
-  for (uint32_t p = DSR_PROG_PAPER_SCALARS; p <= DSR_PROG_WORKERS; ++p)
+  for (uint32_t p = DSR_PROG_PAPER_SCALARS; p <= DSR_PROG_WORKERS + 1; ++p)
     for (uint32_t t : kThreads) {
-      const void *k = reinterpret_cast<const void *>(plain_kernel_for(p, t));
-      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(smem));
+      // the last round: the worker program's shared-memory-table variant
+      const void *k = reinterpret_cast<const void *>(
+          p <= DSR_PROG_WORKERS ? plain_kernel_for(p, t) : plain_kernel_for(DSR_PROG_WORKERS, t, 1));
+      // a kernel with static shared memory of its own can take that much
+      // less dynamic shared memory (a larger slab then fails at launch)
+      cudaFuncAttributes fa{};
+      cudaError_t e = cudaFuncGetAttributes(&fa, k);
+      if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "cudaFuncGetAttributes");
+      const uint32_t room = static_cast<uint32_t>(ctx->max_smem_optin) -
+                            static_cast<uint32_t>(fa.sharedSizeBytes);
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(smem < room ? smem : room));
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared);
@@ -289,7 +299,7 @@ int32_t dsr_launch_plain(dsr_ctx *ctx, const dsr_region_desc *d, const void *ima
                          void *out_dev, dsr_team_status *status_dev, cudaStream_t s) {
   // a team without workers gets one worker warp (its region width is 1)
   const uint32_t block = d->threads > 32u ? d->threads : 64u;
-  KernelFn k = plain_kernel_for(d->program, block);
+  KernelFn k = plain_kernel_for(d->program, block, d->param);
   const uint32_t slab = dsr_plain_slab(ctx, d);
   // programmatic stream serialisation: this grid may be dispatched while the
   // kernel before it in the stream drains (its threads wait for that kernel
@@ -400,7 +410,7 @@ extern "C" int32_t dsr_region_occupancy(dsr_ctx *ctx, const dsr_region_desc *d,
   const char *why;
   if (dsr_check_shape(d, &why) != DSR_OK) return dsr_fail(ctx, DSR_ERR_INVALID, "%s", why);
   const uint32_t block = d->threads > 32u ? d->threads : 64u;
-  const void *k = reinterpret_cast<const void *>(plain_kernel_for(d->program, block));
+  const void *k = reinterpret_cast<const void *>(plain_kernel_for(d->program, block, d->param));
   const uint32_t slab = dsr_plain_slab(ctx, d);
   const uint32_t smem = kCtrlBytes + slab;
   cudaFuncAttributes a{};

@@ -675,7 +675,13 @@ struct ProgHetero {
 // l. A frame's slot reaches the lanes of the nested team by a warp shuffle
 // (the frame table of the warp is a register per lane).
 // ---------------------------------------------------------------------------
-struct ProgWorkers {
+// kSmemShare: the nested teams get their workers' keys and frame-slot
+// offsets from a per-warp table in shared memory (each worker writes its
+// entry, __syncwarp, the lanes read the entry they need) instead of by warp
+// shuffles; the same results, for measuring the two ways of sharing within
+// a warp (a descriptor's param selects it in the plain launch).
+template <bool kSmemShare>
+struct ProgWorkersT {
   static constexpr uint32_t kProgram = DSR_PROG_WORKERS;
   static constexpr bool kDense = false;
   // Teams hold large warp stacks, so few fit an SM: the plain kernel gets
@@ -709,7 +715,7 @@ struct ProgWorkers {
     }
     __syncwarp();
     const uint32_t width = region_width(d);
-    parallel<ProgWorkers>(e, 0, width, 0);
+    parallel<ProgWorkersT>(e, 0, width, 0);
     const Ctrl *c = ctrl();
     s.hwm += c->whwm;
     s.spill += c->wspill;
@@ -755,15 +761,27 @@ struct ProgWorkers {
 
   // Fill of frames l0 .. l1-1 stored back to back (stride fp) from `base`:
   // G_l = image words ^ key of worker l (key_lane: this lane's worker's key).
+  // The key of worker l of the warp (this lane's is key_lane): by shuffle,
+  // or from the warp's table in shared memory.
+  __device__ static uint32_t key_of(uint32_t key_lane, const uint32_t *tab, uint32_t l) {
+    if constexpr (kSmemShare) return tab[l];
+    return __shfl_sync(0xffffffffu, key_lane, l);
+  }
+  __device__ static uint32_t off_of(uint32_t off_lane, const uint32_t *tab, uint32_t l) {
+    if constexpr (kSmemShare) return tab[32u + l];
+    return __shfl_sync(0xffffffffu, off_lane, l);
+  }
+
   template <bool kSmem>
   __device__ static void fill_phase(uint8_t *base, uint32_t fp, uint32_t l0, uint32_t l1,
-                                    uint32_t L, const uint4 *img4, uint32_t key_lane) {
+                                    uint32_t L, const uint4 *img4, uint32_t key_lane,
+                                    const uint32_t *tab) {
     const uint32_t nv = L / 4u, tw = L - 4u * nv;
     if (nv) {
       const uint32_t total = (l1 - l0) * nv;
       Walk it(l0, nv);
       for (uint32_t i = lane_id(); i < ((total + 31u) & ~31u); i += 32u, it.next()) {
-        const uint32_t key = __shfl_sync(0xffffffffu, key_lane, it.l & 31u);
+        const uint32_t key = key_of(key_lane, tab, it.l & 31u);
         if (i < total) {
           uint4 x = __ldg(img4 + it.q);
           x.x ^= key;
@@ -779,7 +797,7 @@ struct ProgWorkers {
       const uint32_t *imgw = reinterpret_cast<const uint32_t *>(img4) + 4u * nv;
       Walk it(l0, tw);
       for (uint32_t i = lane_id(); i < ((total + 31u) & ~31u); i += 32u, it.next()) {
-        const uint32_t key = __shfl_sync(0xffffffffu, key_lane, it.l & 31u);
+        const uint32_t key = key_of(key_lane, tab, it.l & 31u);
         if (i < total)
           reinterpret_cast<uint32_t *>(base + (it.l - l0) * fp)[4u * nv + it.q] =
               __ldg(imgw + it.q) ^ key;
@@ -794,7 +812,7 @@ struct ProgWorkers {
   // frame's words is paid once per four.
   template <bool kSmem>
   __device__ static void nested_phase(uint8_t *base, uint32_t l0, uint32_t l1, uint32_t L,
-                                      uint32_t s1, uint32_t off_lane) {
+                                      uint32_t s1, uint32_t off_lane, const uint32_t *tab) {
     constexpr uint32_t kB = 4;
     if ((L & 31u) == 0) {
       // L a multiple of 32: the frames lie back to back (a frame's slot is
@@ -827,7 +845,7 @@ struct ProgWorkers {
       uint32_t v[kB], w[kB];
 #pragma unroll
       for (uint32_t u = 0; u < kB; ++u) {
-        const uint32_t off = __shfl_sync(0xffffffffu, off_lane, it.l & 31u);
+        const uint32_t off = off_of(off_lane, tab, it.l & 31u);
         g[u] = i + 32u * u < total ? reinterpret_cast<uint32_t *>(base + off) + it.q : nullptr;
         w[u] = it.q;
         v[u] = g[u] ? *g[u] : 0u;
@@ -886,12 +904,21 @@ struct ProgWorkers {
     // each worker's key and its frame's slot offset in its share
     const uint32_t key = mix32(s0 + t0 + lane);
     const uint32_t off = lane < in_slab ? lane * fp : (lane - in_slab) * fp;
+    const uint32_t *tab = nullptr;
+    if constexpr (kSmemShare) {
+      // the warp's table: key of worker l at [l], its slot offset at [32 + l]
+      __shared__ uint32_t share[DSR_MAX_THREADS / 32][64];
+      share[warp][lane] = key;
+      share[warp][32u + lane] = off;
+      __syncwarp();
+      tab = share[warp];
+    }
     // the workers' sequential parts: their fills (order-free word copies)
-    fill_phase<true>(sbase, fp, 0, in_slab, L, img4, key);
-    if (pushed > in_slab) fill_phase<false>(gbase, fp, in_slab, pushed, L, img4, key);
+    fill_phase<true>(sbase, fp, 0, in_slab, L, img4, key, tab);
+    if (pushed > in_slab) fill_phase<false>(gbase, fp, in_slab, pushed, L, img4, key, tab);
     __syncwarp();  // fork of the nested regions
-    nested_phase<true>(sbase, 0, in_slab, L, s1, off);
-    if (pushed > in_slab) nested_phase<false>(gbase, in_slab, pushed, L, s1, off);
+    nested_phase<true>(sbase, 0, in_slab, L, s1, off, tab);
+    if (pushed > in_slab) nested_phase<false>(gbase, in_slab, pushed, L, s1, off, tab);
     __syncwarp();  // join
     if (lane < pushed) {
       const uint32_t sum = lane < in_slab ? frame_sum_own(sbase + off, L)
@@ -905,5 +932,8 @@ struct ProgWorkers {
 
   __device__ static void body(const Env &, uint32_t, uint32_t, uint32_t, uint32_t) {}
 };
+
+using ProgWorkers = ProgWorkersT<false>;
+using ProgWorkersSmem = ProgWorkersT<true>;
 
 }  // namespace dsr

@@ -248,6 +248,30 @@ def test_workers_parity(rt, teams, threads, S, width):
     assert (gs["status"] == 0).all() and (gs["depth_final"] == 0).all()
 
 
+@pytest.mark.parametrize("teams,threads,S,width,slab_frames", [
+    (4, 160, 100, 45, 32),   # the general walk (keys and offsets per step)
+    (2, 1024, 36, 0, 32),    # 31 worker warps
+    (5, 256, 256, 0, 32),    # rows of 32 words (keys only)
+    (3, 192, 200, 70, 9),    # part of each warp's frames on the overflow share
+])
+def test_workers_smem_table_sharing_equals_shuffles(rt, teams, threads, S, width, slab_frames):
+    """The worker program with the nested teams' keys and frame offsets read
+    from a shared-memory table (param 1) against the oracle and against the
+    shuffle variant (param 0): the same outputs and team records."""
+    slab = _workers_slab(threads, S, slab_frames)
+    ovf = (threads - 32) * ((S + 15) // 16 * 16)
+    outs = []
+    for share in (0, 1):
+        work = wl.workers(teams=teams, threads=threads, frame_bytes=S, width=width, share=share)
+        g, gs, r, rs = _run_both(rt, work, slab=slab, ovf=ovf, max_teams=teams)
+        assert _same_out(g, r)
+        _assert_status_equal(gs, rs)
+        outs.append((g, gs))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    for f in ("status", "hwm_bytes", "spill_bytes", "chk"):
+        assert np.array_equal(outs[0][1][f], outs[1][1][f]), f
+
+
 @pytest.mark.parametrize("S", [200, 256])  # frames of 50 words; of two rows of 32
 def test_workers_spill_to_overflow_shares(rt, S):
     fp = (S + 15) // 16 * 16

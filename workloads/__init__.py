@@ -313,13 +313,16 @@ def hetero(n_instances: int = 10000, seed: int = DEFAULT_SEED,
 # Worker-level sharing (the paper's future work, Sec. 7)
 # ----------------------------------------------------------------------------
 def workers(teams: int = 1024, threads: int = 256, frame_bytes: int = 256, width: int = 0,
-            seed: int = DEFAULT_SEED) -> Workload:
+            seed: int = DEFAULT_SEED, share: int = 0) -> Workload:
     """Per team an image of int32 s[4] then int32 base[S/4], the pair padded
-    to 16 bytes; uniform int32 words."""
+    to 16 bytes; uniform int32 words. `share` is the descriptor's param: how
+    the nested teams get their workers' keys and frame offsets on the GPU
+    (0: warp shuffles, 1: a shared-memory table); results do not depend on
+    it."""
     assert frame_bytes % 4 == 0 and frame_bytes > 0 and threads >= 64
     stride = 16 + _pad16(frame_bytes)
     img = uniform_u32(derive(seed, 7, frame_bytes), teams * stride // 4)
-    r = Region(PROG_WORKERS, teams, threads, 2, [16, frame_bytes], width=width)
+    r = Region(PROG_WORKERS, teams, threads, 2, [16, frame_bytes], width=width, param=share)
     return Workload("workers", [r], _as_bytes(img), 4 * teams * r.team_width, teams)
 
 

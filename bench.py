@@ -715,7 +715,7 @@ def measure_served(dsr, rt, dist=None):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="dsr", choices=["dsr", "reference"])
     ap.add_argument("--workload", default="nested")

@@ -337,6 +337,26 @@ int32_t dsr_launch_batch(dsr_ctx *ctx, const dsr_region_desc *descs_dev, uint32_
 int32_t dsr_batch_errors(dsr_ctx *ctx, const void *workspace_dev, uint32_t *errors,
                          uint64_t *tasks_counted, void *stream);
 
+/* Ask the batch running on workspace_dev (NULL: the static workspace of
+ * dsr_launch_batch_static on the ctx's device) to stop early: each of its
+ * CTAs takes no further task after its next grab (a few tasks at most), so
+ * a batch with a pathological instance can be drained without waiting out
+ * every task. The flag is written by a host-to-device copy on a stream of
+ * the ctx (a copy engine, since the persistent kernel holds every SM); the
+ * call does not wait. It stops a batch that is running: a launch clears the
+ * flag when its scan starts, so call it after the launch has begun (a batch
+ * still queued behind other work may miss it). Teams that never ran keep
+ * whatever their status words held; dsr_batch_progress says how many tasks
+ * were taken. Errors: DSR_ERR_INVALID, DSR_ERR_CUDA. */
+int32_t dsr_batch_abort(dsr_ctx *ctx, void *workspace_dev);
+
+/* After a batch completed (synchronises `stream`): tasks its CTAs took (ran,
+ * or rejected as invalid) and tasks its scan counted; fewer taken than
+ * counted means the batch was stopped by dsr_batch_abort. workspace_dev
+ * NULL: the static workspace. */
+int32_t dsr_batch_progress(dsr_ctx *ctx, const void *workspace_dev, uint64_t *tasks_taken,
+                           uint64_t *tasks_counted, void *stream);
+
 /* Autotuner: runs the batch once per candidate CTA shape (64..512
  * threads) and slab size (2..32 KB), each at the most resident CTAs per SM
  * that fit, and returns the fastest in *best (and its time in *best_ms).

@@ -128,7 +128,9 @@ constexpr uint32_t kBuckets = 32;  // cost classes, log2 of a team's estimated c
 struct WsHeader {
   unsigned long long total;  // tasks counted by the scan
   unsigned int errors;       // tasks rejected on the device
-  unsigned int pad[29];
+  unsigned int abort;        // set by the host (dsr_batch_abort): take no more tasks
+  unsigned int ran;          // tasks the CTAs ran (added up as they leave)
+  unsigned int pad[27];
   unsigned long long bucket_fill[kBuckets];  // next free task slot of each cost class
   struct {
     unsigned long long next;  // tasks of this part handed out
@@ -152,15 +154,24 @@ struct Feeder {
 
   // Next chunk of tasks of the current part: positions [*start, *end) of
   // the part (task index = g + position * kGroups); *start == *end when no
-  // task is left anywhere.
+  // task is left anywhere, or when the host has asked the batch to stop
+  // (the flag is read with each grab, in the same round trip).
   __device__ __forceinline__ void next(WsHeader *hdr, uint32_t total, uint32_t *start,
                                        uint32_t *end) {
     while (visited < kGroups) {
       const uint32_t count = g < total ? (total - g + kGroups - 1) / kGroups : 0u;
       unsigned long long t = 0;
-      if (lane_id() == 0)
+      uint32_t stop = 0;
+      if (lane_id() == 0) {
         t = atomicAdd(&hdr->cursor[g].next, static_cast<unsigned long long>(kGrab));
+        stop = *reinterpret_cast<volatile const unsigned int *>(&hdr->abort);
+      }
       t = __shfl_sync(0xffffffffu, t, 0);
+      if (__shfl_sync(0xffffffffu, stop, 0)) {
+        *start = *end = 0;
+        visited = kGroups;
+        return;
+      }
       if (t < count) {
         *start = static_cast<uint32_t>(t);
         *end = min(*start + kGrab, count);
@@ -209,6 +220,7 @@ __global__ void __launch_bounds__(MAXT, MINB) batch_kernel(const __grid_constant
   uint32_t cached = 0xffffffffu;  // instance whose descriptor is in the control block
   bool cached_ok = false;
   bool first = true;
+  uint32_t ran = 0;
   while (have) {
     // the next task: its chunk grab (at a chunk boundary) and its entry
     uint32_t nxt = cur + 1, nend = end;
@@ -245,11 +257,13 @@ __global__ void __launch_bounds__(MAXT, MINB) batch_kernel(const __grid_constant
       P::master(e, s);
       team_report(e, s, status);
     }
+    ++ran;
     cur = nxt;
     end = nend;
     task = ntask;
     have = nhave;
   }
+  if (lane == 0 && ran) atomicAdd(&hdr->ran, ran);
   terminate_workers();
 }
 

@@ -156,6 +156,8 @@ def _declare(L):
                                            _vp, _u64, P(dsr_batch_tuning), _vp]),
         "dsr_batch_static_capacity": (_u64, []),
         "dsr_batch_static_errors": (_i32, [_vp, P(_u32), P(_u64), _vp]),
+        "dsr_batch_abort": (_i32, [_vp, _vp]),
+        "dsr_batch_progress": (_i32, [_vp, _vp, P(_u64), P(_u64), _vp]),
         "dsr_report_error": (_i32, [_vp, _i32, ctypes.c_char_p]),
         "dsr_user_plain_config": (_i32, [_vp, P(dsr_region_desc), _u64, _u64, _u64, _u64, _u64,
                                          _vp, _vp, P(dsr_plain_config)]),
@@ -202,7 +204,8 @@ def exported_symbols():
             "dsr_batch_workspace_bytes",
             "dsr_batch_count", "dsr_launch_batch", "dsr_batch_errors", "dsr_autotune",
             "dsr_launch_regions", "dsr_launch_batch_static", "dsr_batch_static_capacity",
-            "dsr_batch_static_errors", "dsr_report_error", "dsr_user_plain_config",
+            "dsr_batch_static_errors", "dsr_batch_abort", "dsr_batch_progress",
+            "dsr_report_error", "dsr_user_plain_config",
             "dsr_batch_prepare",
             "dsr_serve_workspace_bytes", "dsr_serve_start",
             "dsr_serve_submit", "dsr_serve_poll", "dsr_serve_stop", "dsr_serve_stats",
@@ -442,6 +445,20 @@ def dsr_probe_smem_bandwidth(ctx: int, reps: int, scratch, stream=None) -> dict:
     _check(lib().dsr_probe_smem_bandwidth(ctx, reps, _ptr(scratch), _stream(stream),
                                           ctypes.byref(r)), ctx)
     return {f: getattr(r, f) for f, _ in dsr_smem_probe._fields_}
+
+
+def dsr_batch_abort(ctx: int, workspace=None) -> None:
+    """Ask the batch running on `workspace` (None: the static workspace) to
+    stop after its CTAs' next grabs; does not wait."""
+    _check(lib().dsr_batch_abort(ctx, _ptr(workspace)), ctx)
+
+
+def dsr_batch_progress(ctx: int, workspace=None, stream=None):
+    """(tasks taken, tasks counted) of the last batch on `workspace`."""
+    t, c = _u64(), _u64()
+    _check(lib().dsr_batch_progress(ctx, _ptr(workspace), ctypes.byref(t), ctypes.byref(c),
+                                    _stream(stream)), ctx)
+    return int(t.value), int(c.value)
 
 
 def dsr_report_error(ctx: int, code: int, msg: str) -> int:

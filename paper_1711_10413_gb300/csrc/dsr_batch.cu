@@ -68,6 +68,8 @@ __global__ void __launch_bounds__(1024) batch_scan(const dsr_region_desc *__rest
     }
     hdr->total = base;
     hdr->errors = 0;
+    hdr->abort = 0;
+    hdr->ran = 0;
   }
   if (tid < kGroups) hdr->cursor[tid].next = 0;
 }
@@ -131,6 +133,8 @@ struct GraphKey {
 
 struct dsr_batch_state {
   cudaStream_t capture = nullptr;
+  cudaStream_t abort_stream = nullptr;  // carries abort flags while a batch holds the SMs
+  unsigned int *abort_one = nullptr;    // pinned host word holding 1
   struct Entry {
     GraphKey key;
     cudaGraphExec_t exec;
@@ -148,6 +152,8 @@ void dsr_ctx_release(dsr_ctx *ctx) {
   if (ctx->batch) {
     drop_graphs(ctx->batch);
     if (ctx->batch->capture) cudaStreamDestroy(ctx->batch->capture);
+    if (ctx->batch->abort_stream) cudaStreamDestroy(ctx->batch->abort_stream);
+    if (ctx->batch->abort_one) cudaFreeHost(ctx->batch->abort_one);
     delete ctx->batch;
     ctx->batch = nullptr;
   }
@@ -418,6 +424,50 @@ extern "C" int32_t dsr_batch_errors(dsr_ctx *ctx, const void *workspace_dev, uin
   return DSR_OK;
 }
 
+// Stop a running batch: its CTAs take no task after their next grab. The
+// flag goes in by a host-to-device copy on a stream of its own (a copy
+// engine writes it while the persistent kernel holds every SM); the call
+// does not wait for it.
+static void *static_ws_of(dsr_ctx *ctx);
+
+extern "C" int32_t dsr_batch_abort(dsr_ctx *ctx, void *workspace_dev) {
+  if (!ctx) return dsr_fail(nullptr, DSR_ERR_INVALID, "null ctx");
+  int32_t rc = dsr_check_device(ctx);
+  if (rc != DSR_OK) return rc;
+  void *ws = workspace_dev ? workspace_dev : static_ws_of(ctx);
+  if (!ws) return dsr_fail(ctx, DSR_ERR_INVALID, "no workspace (no static batch has run)");
+  dsr_batch_state *b = batch_state(ctx);
+  cudaError_t e = cudaSuccess;
+  if (!b->abort_stream) e = cudaStreamCreateWithFlags(&b->abort_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !b->abort_one) {
+    e = cudaHostAlloc(&b->abort_one, sizeof(unsigned int), cudaHostAllocDefault);
+    if (e == cudaSuccess) *b->abort_one = 1u;
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&static_cast<WsHeader *>(ws)->abort, b->abort_one, sizeof(unsigned int),
+                        cudaMemcpyHostToDevice, b->abort_stream);
+  if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "batch abort");
+  return DSR_OK;
+}
+
+extern "C" int32_t dsr_batch_progress(dsr_ctx *ctx, const void *workspace_dev,
+                                      uint64_t *tasks_taken, uint64_t *tasks_counted,
+                                      void *stream) {
+  if (!ctx || !tasks_taken) return dsr_fail(ctx, DSR_ERR_INVALID, "null argument");
+  int32_t rc = dsr_check_device(ctx);
+  if (rc != DSR_OK) return rc;
+  const void *ws = workspace_dev ? workspace_dev : static_ws_of(ctx);
+  if (!ws) return dsr_fail(ctx, DSR_ERR_INVALID, "no workspace (no static batch has run)");
+  WsHeader h;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(&h, ws, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "workspace read");
+  *tasks_taken = h.ran;
+  if (tasks_counted) *tasks_counted = h.total;
+  return DSR_OK;
+}
+
 // Autotuner: time every candidate CTA shape x slab size on the real batch
 // (outputs are the same for every candidate) and keep the fastest.
 extern "C" int32_t dsr_autotune(dsr_ctx *ctx, const dsr_region_desc *descs_dev, uint32_t n,
@@ -524,6 +574,11 @@ int32_t static_setup(dsr_ctx *ctx, void **ws) {
 }  // namespace
 
 extern "C" uint64_t dsr_batch_static_capacity(void) { return kStaticWsBytes; }
+
+static void *static_ws_of(dsr_ctx *ctx) {
+  std::lock_guard<std::mutex> g(g_static_mu);
+  return ctx->device >= 0 && ctx->device < kMaxDevices ? g_static_ptr[ctx->device] : nullptr;
+}
 
 extern "C" int32_t dsr_launch_batch_static(dsr_ctx *ctx, const dsr_region_desc *descs_dev,
                                            uint32_t n, uint32_t program, uint64_t total_teams,

@@ -195,3 +195,12 @@ def test_user_program_library_builds_and_exports(L):
     r.program = 200   # neither built in nor in the user range
     with pytest.raises(dsr.DsrError):
         dsr.dsr_region_extent(r)
+
+
+def test_batch_abort_and_progress_refuse_without_ctx(L):
+    """Host-side refusals of the abort and progress calls (no GPU touched)."""
+    import ctypes
+    assert dsr.lib().dsr_batch_abort(None, None) == dsr.DSR_ERR_INVALID
+    t = ctypes.c_uint64()
+    assert dsr.lib().dsr_batch_progress(None, None, ctypes.byref(t), None, None) == \
+        dsr.DSR_ERR_INVALID

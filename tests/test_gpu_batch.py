@@ -222,3 +222,61 @@ def test_batch_sweep_streams_across_tasks():
             assert (np.abs(got.astype(np.float64) - s64.reshape(T, W)) <= tol).all()
     finally:
         rt.close()
+
+
+def test_batch_abort_stops_a_running_batch():
+    """dsr_batch_abort on a running 10,000-instance batch: its CTAs stop taking
+    tasks, fewer tasks are taken than counted, every team that ran has the
+    same output row and record as in a full run, the others were not
+    touched, and the next launch on the same workspace runs to completion
+    (the scan clears the flag)."""
+    import time
+
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1711_10413_gb300 as dsr
+    rt = dsr.Runtime(0, slab_bytes=16384, overflow_bytes_per_team=3 * 32768, max_teams=4096)
+    try:
+        work = wl.hetero(n_instances=10000)
+        b = rt.batch_buffers(work)
+        tuning = dict(threads=128, slab_bytes=8192, ctas_per_sm=0)
+        rt.launch_batch(b, tuning)
+        torch.cuda.synchronize()
+        full_out = b["out"].cpu().numpy().copy()
+        full_st = b["status"].cpu().numpy().view(dsr.TEAM_STATUS_DTYPE).copy()
+        assert dsr.dsr_batch_progress(rt.ctx, b["ws"]) == (b["total"], b["total"])
+        b["out"].fill_(-7)
+        b["status"].fill_(-1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rt.launch_batch(b, tuning)
+        time.sleep(0.002)   # the batch takes about 5 ms
+        dsr.dsr_batch_abort(rt.ctx, b["ws"])
+        torch.cuda.synchronize()
+        elapsed = time.perf_counter() - t0
+        taken, counted = dsr.dsr_batch_progress(rt.ctx, b["ws"])
+        assert counted == b["total"] and 0 < taken < counted, (taken, counted, elapsed)
+        st = b["status"].cpu().numpy().view(dsr.TEAM_STATUS_DTYPE)
+        out = b["out"].cpu().numpy()
+        ran = st["status"] != -1
+        assert int(ran.sum()) == taken
+        for f in ("status", "depth_final", "hwm_bytes", "chk"):
+            assert np.array_equal(st[f][ran], full_st[f][ran]), f
+        # element mask: team t of an instance owns W' consecutive output words
+        mask = np.zeros(out.size, dtype=bool)
+        covered = np.zeros(out.size, dtype=bool)
+        for r in work.regions:
+            W, o0 = r.team_width, r.out_offset // 4
+            mask[o0:o0 + r.teams * W] = np.repeat(ran[r.status_index:r.status_index + r.teams], W)
+            covered[o0:o0 + r.teams * W] = True
+        assert np.array_equal(out[mask], full_out[mask])
+        assert (out[covered & ~mask] == -7).all()
+        # the next launch runs everything
+        rt.launch_batch(b, tuning)
+        torch.cuda.synchronize()
+        assert dsr.dsr_batch_progress(rt.ctx, b["ws"]) == (b["total"], b["total"])
+        again = b["out"].cpu().numpy()
+        assert np.array_equal(again[covered], full_out[covered])  # padding between rows aside
+    finally:
+        rt.close()

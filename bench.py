@@ -59,10 +59,11 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 ROTATE_BYTES = 264 << 20    # > twice the 129 MB L2: the headline's rotating input sets
 
 # CTA shapes of the device-resident server (threads per CTA, shared slab
-# bytes), from sweeps of 96 to 512 threads and 8 to 32 KiB slabs on the
+# bytes), from sweeps of 64 to 256 threads and 4 to 24 KiB slabs on the
 # hetero distribution: 256 threads gives the lowest latency, 128 threads
-# with 8 KiB slabs (the most resident CTAs) the highest capacity.
-SERVE_SHAPES = [dict(threads=256, slab_bytes=16384), dict(threads=128, slab_bytes=8192)]
+# with 24 KiB slabs the highest capacity (above a million requests/s) with
+# latency close behind.
+SERVE_SHAPES = [dict(threads=256, slab_bytes=16384), dict(threads=128, slab_bytes=24576)]
 
 # DRAM traffic per launch of the plain nested kernel in the headline's steady
 # state (launches back to back over the rotating input sets, so each launch

@@ -33,6 +33,18 @@
  *     __device__ static void body(const dsr_thread &thr);  // one thread of a
  *   };                                                      // parallel region
  *
+ * Optionally, a plain launch's inputs can be pulled into L2 before the
+ * kernel waits for the work queued ahead of it in the stream (programmatic
+ * dependent launch lets its CTAs start while that work finishes):
+ *
+ *     __device__ static void prefetch(const dsr_region_desc &d,
+ *                                     const uint8_t *images, uint32_t team);
+ *
+ * runs on one lane of each team's master warp before that wait and may only
+ * call dsr_prefetch_l2 (hints that change no value a load returns): it must
+ * not read or write global memory, since what the earlier work writes is
+ * not visible yet.
+ *
  * and is launched with dsr_launch_user_region<MyProgram> (one CTA per team,
  * one launch per region, Sec. 4) or dsr_launch_user_batch<MyProgram> (many
  * region instances in one persistent launch), which instantiate the same
@@ -98,6 +110,13 @@ __device__ __forceinline__ uint32_t dsr_lane() { return dsr::lane_id(); }
 
 /* True in the master thread: lane 0 of the master warp (Sec. 4). */
 __device__ __forceinline__ bool dsr_is_master() { return dsr::lane_id() == 0; }
+
+/* Hint: pull [src, src + nbytes) of global memory into L2 (one bulk
+ * prefetch per 64 KiB; src 16-byte aligned and nbytes a multiple of 16, else
+ * nothing is done). No completion, no effect on any value a load returns. */
+__device__ __forceinline__ void dsr_prefetch_l2(const void *src, uint32_t nbytes) {
+  dsr::prefetch_l2(src, nbytes);
+}
 
 /* Orders the master warp's lanes: writes a lane made before it are visible
  * to the others after it. */
@@ -211,9 +230,17 @@ __device__ __forceinline__ uint8_t *dsr_out(const dsr_thread &w) { return w.e->o
 
 namespace dsr {
 
+// The program's optional prefetch, under the name the plain kernel looks for.
+template <class U, class = void>
+struct UserPrefetch {};
+template <class U>
+struct UserPrefetch<U, std::void_t<decltype(&U::prefetch)>> {
+  __device__ static void prefetch_inputs(const Env &e) { U::prefetch(*e.d, e.images, e.team); }
+};
+
 // A user program seen through the interface the kernels call.
 template <class U>
-struct UserProgram {
+struct UserProgram : UserPrefetch<U> {
   static constexpr uint32_t kProgram = U::kProgram;
   static constexpr bool kDense = false;
   static constexpr bool kUser = true;

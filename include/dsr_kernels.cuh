@@ -40,6 +40,16 @@ struct wide_regs : std::false_type {};
 template <class P>
 struct wide_regs<P, std::void_t<decltype(P::kWideRegs)>> : std::bool_constant<P::kWideRegs> {};
 
+// Programs whose teams' input ranges follow from the descriptor alone name
+// them in P::prefetch_inputs(e), which the plain kernel issues as L2
+// prefetches before it waits for the previous launch: a prefetch is a hint
+// with no effect on what any load returns, so it may run before the inputs
+// are final, and the team's first reads then come from L2.
+template <class P, class = void>
+struct has_prefetch : std::false_type {};
+template <class P>
+struct has_prefetch<P, std::void_t<decltype(&P::prefetch_inputs)>> : std::true_type {};
+
 // Images, outputs and statuses of a well-formed descriptor of program P.
 template <class P>
 DSR_HD void program_extent(const dsr_region_desc &d, uint64_t *ib, uint64_t *ob, uint64_t *ns) {
@@ -90,6 +100,9 @@ __global__ void __launch_bounds__(MAXT, MINB)
   team_setup(s, slab_bytes,
              ovf_per_team ? pool + static_cast<uint64_t>(blockIdx.x) * ovf_per_team : nullptr,
              ovf_per_team, timeout_ns, true);
+  if constexpr (has_prefetch<P>::value) {
+    if (lane_id() == 0) P::prefetch_inputs(e);
+  }
   wait_prerequisites();  // the set-up above touches shared memory only
   P::master(e, s);
   terminate_workers();

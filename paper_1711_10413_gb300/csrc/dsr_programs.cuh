@@ -237,6 +237,9 @@ struct ProgNested {
     }
   }
 
+  // All D level images of the team (plain kernel, before the wait).
+  __device__ static void prefetch_inputs(const Env &e) { prefetch_l2(image(e, 1), e.d->depth * 1088u); }
+
   // The image of level k of this team (1088 bytes).
   __device__ static const uint8_t *image(const Env &e, uint32_t k) {
     return e.images + e.d->image_offset +
@@ -365,6 +368,14 @@ struct ProgNested {
 struct ProgSweep {
   static constexpr uint32_t kProgram = DSR_PROG_SWEEP;
   static constexpr bool kDense = false;
+  // The team's image (plain kernel, before the wait), for frames of up to
+  // 32 KiB: a launch's larger images (up to 100 MB at 192 KiB) prefetched at
+  // once contend with the fills and ran slower.
+  __device__ static void prefetch_inputs(const Env &e) {
+    const uint32_t S = e.d->frame_bytes[0];
+    if (S <= 32768u)
+      prefetch_l2(e.images + e.d->image_offset + static_cast<uint64_t>(e.team) * S, S & ~15u);
+  }
   __device__ static void master(const Env &e, Stack &s) {
     const dsr_region_desc &d = *e.d;
     const uint32_t S = d.frame_bytes[0];
@@ -447,6 +458,16 @@ struct ProgHetero {
   static constexpr uint32_t kProgram = DSR_PROG_HETERO;
   static constexpr bool kDense = false;
   enum : uint32_t { kUpdate = 0, kInner = 1 };
+
+  // The instance's level images (plain kernel, before the wait). Every team
+  // reads the same images, so team 0 alone asks for them.
+  __device__ static void prefetch_inputs(const Env &e) {
+    if (e.team != 0) return;
+    uint32_t total = 0;
+    for (uint32_t k = 0; k < e.d->depth && k < DSR_MAX_DEPTH; ++k)
+      total += (e.d->frame_bytes[k] + 15u) & ~15u;
+    prefetch_l2(e.images + e.d->image_offset, total);
+  }
 
   __device__ static void master(const Env &e, Stack &s) {
     const dsr_region_desc &d = *e.d;

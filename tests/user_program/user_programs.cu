@@ -99,6 +99,14 @@ struct UserHetero {
     *out_bytes = 4ull * d.teams * user_width(d);
   }
 
+  // the instance's images towards L2 before the launch waits (team 0 asks
+  // for them; every team reads the same ones)
+  __device__ static void prefetch(const dsr_region_desc &d, const uint8_t *images, uint32_t team) {
+    uint64_t ib, ob;
+    extent(d, &ib, &ob);
+    if (team == 0) dsr_prefetch_l2(images + d.image_offset, static_cast<uint32_t>(ib));
+  }
+
   __device__ static void master(dsr_team &t) {
     const dsr_region_desc &d = dsr_desc(t);
     const uint32_t D = d.depth, team = dsr_team_num(t), lane = dsr_lane();
@@ -152,6 +160,10 @@ struct UserHetero {
 };
 
 }  // namespace
+
+// The plain kernel finds the optional prefetch through the adapter.
+static_assert(dsr::has_prefetch<dsr::UserProgram<UserHetero>>::value, "prefetch hook");
+static_assert(!dsr::has_prefetch<dsr::UserProgram<UserPaperScalars>>::value, "no prefetch hook");
 
 // ---- C entry points the tests call (ctypes) -------------------------------
 #define USER_ENTRY(name, Prog)                                                                 \

@@ -495,7 +495,7 @@ int32_t dsr_batch_prepare(dsr_ctx *ctx, const dsr_region_desc *descs_dev, uint32
  * batching). All requests share the buffers named here; each request's
  * descriptor offsets index them. */
 typedef struct dsr_serve_cfg {
-  uint32_t program;          /* DSR_PROG_SCALARS, _NESTED or _HETERO */
+  uint32_t program;          /* DSR_PROG_SCALARS, _NESTED or _HETERO (a user id: dsr_serve_start_user) */
   uint32_t threads;          /* server CTA threads, multiple of 32 in [64, 1024] */
   uint32_t slab_bytes;       /* shared-memory slab per CTA, multiple of 16 */
   uint32_t ctas_per_sm;      /* 0 = as many as fit */
@@ -521,6 +521,42 @@ uint64_t dsr_serve_workspace_bytes(uint32_t capacity);
  * poll. Errors: DSR_ERR_INVALID, DSR_ERR_BUDGET (workspace), DSR_ERR_CUDA. */
 int32_t dsr_serve_start(dsr_ctx *ctx, const dsr_serve_cfg *cfg, void *workspace_dev,
                         uint64_t workspace_bytes);
+
+/* A user-written program's server (include/dsr_device.cuh,
+ * dsr_serve_user_start, fills this in): the library runs the host side of
+ * the served form and calls these hooks, which live in the user's
+ * translation unit with the program's server kernel. */
+typedef struct dsr_serve_program {
+  uint32_t program;  /* the program's descriptor id, >= DSR_PROG_USER */
+  uint32_t reserved; /* 0 */
+  /* Host-side check of one request against the server's buffers: DSR_OK,
+   * or DSR_ERR_INVALID when the descriptor is malformed or indexes past
+   * image_bytes / out_bytes / n_status. */
+  int32_t (*validate)(const dsr_region_desc *d, uint64_t image_bytes, uint64_t out_bytes,
+                      uint64_t n_status);
+  /* Set the server kernel's shared-memory limit for CTAs of `threads`
+   * threads and `smem_bytes` of dynamic shared memory on the current
+   * device, and give its resident CTAs per SM (0: the shape does not fit).
+   * DSR_OK or DSR_ERR_CUDA. */
+  int32_t (*prepare)(uint32_t threads, uint32_t smem_bytes, int32_t *ctas_per_sm);
+  /* Launch the server kernel: `grid` CTAs of `threads` threads with
+   * `smem_bytes` of dynamic shared memory on `stream`, its one argument the
+   * block at `args` (the library's server arguments, the ServeArgs layout of
+   * include/dsr_serve_kernel.cuh). DSR_OK or DSR_ERR_CUDA. */
+  int32_t (*launch)(const void *args, uint32_t grid, uint32_t threads, uint32_t smem_bytes,
+                    void *stream);
+} dsr_serve_program;
+
+/* dsr_serve_start for a user-written program: cfg->program must equal
+ * prog->program (>= DSR_PROG_USER) and every hook must be set; the
+ * program's own validate hook checks each submitted descriptor. Admission
+ * counts a request's spill from its descriptor's depth and frame_bytes as
+ * for the built-in programs. Everything else (rings, workspace, submit,
+ * poll, stop, stats, bench) as dsr_serve_start. The hooks must stay valid
+ * until the server is stopped and released (dsr_destroy). Errors as
+ * dsr_serve_start. */
+int32_t dsr_serve_start_user(dsr_ctx *ctx, const dsr_serve_cfg *cfg, void *workspace_dev,
+                             uint64_t workspace_bytes, const dsr_serve_program *prog);
 
 /* Submit one region instance (non-blocking). The descriptor is checked on
  * the host. Admission: the request needs a free ring slot and, for its

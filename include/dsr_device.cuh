@@ -46,9 +46,11 @@
  * not visible yet.
  *
  * and is launched with dsr_launch_user_region<MyProgram> (one CTA per team,
- * one launch per region, Sec. 4) or dsr_launch_user_batch<MyProgram> (many
- * region instances in one persistent launch), which instantiate the same
- * kernels the built-in programs run.
+ * one launch per region, Sec. 4), dsr_launch_user_batch<MyProgram> (many
+ * region instances in one persistent launch) or served with
+ * dsr_serve_user_start<MyProgram> (a device-resident server fed by
+ * dsr_serve_submit), which instantiate the same kernels the built-in
+ * programs run.
  *
  * Execution model.
  *  - master() runs on the 32 lanes of the team's master warp together (the
@@ -87,6 +89,7 @@
 
 #include "dsr.h"
 #include "dsr_kernels.cuh"
+#include "dsr_serve_kernel.cuh"
 
 /* The master's handle on its team (master side only). */
 struct dsr_team {
@@ -383,6 +386,62 @@ int32_t dsr_launch_user_batch(dsr_ctx *ctx, const dsr_region_desc *descs_dev, ui
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return dsr_report_error(ctx, DSR_ERR_CUDA, cudaGetErrorString(e));
   return DSR_OK;
+}
+
+namespace dsr {
+
+// The hooks through which the library's served form runs user program U:
+// the descriptor check, the kernel's attributes and occupancy, and the
+// server launch, all in the user's translation unit.
+template <class U>
+struct UserServer {
+  using P = UserProgram<U>;
+  static int32_t validate(const dsr_region_desc *d, uint64_t image_bytes, uint64_t out_bytes,
+                          uint64_t n_status) {
+    return d && program_fits<P>(*d, image_bytes, out_bytes, n_status) ? DSR_OK : DSR_ERR_INVALID;
+  }
+  static int32_t prepare(uint32_t threads, uint32_t smem_bytes, int32_t *ctas_per_sm) {
+    *ctas_per_sm = 0;
+    const void *k = reinterpret_cast<const void *>(pick_serve<P>(threads));
+    int device = 0, occ = 0;
+    if (cudaGetDevice(&device) != cudaSuccess ||
+        ensure_smem_limit(k, device, smem_bytes) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, static_cast<int>(threads),
+                                                      smem_bytes) != cudaSuccess)
+      return DSR_ERR_CUDA;
+    *ctas_per_sm = occ;
+    return DSR_OK;
+  }
+  static int32_t launch(const void *args, uint32_t grid, uint32_t threads, uint32_t smem_bytes,
+                        void *stream) {
+    pick_serve<P>(threads)<<<grid, threads, smem_bytes, static_cast<cudaStream_t>(stream)>>>(
+        *static_cast<const ServeArgs *>(args));
+    // the library reads (and clears) the error itself
+    return cudaPeekAtLastError() == cudaSuccess ? DSR_OK : DSR_ERR_CUDA;
+  }
+};
+
+}  // namespace dsr
+
+/* Serve user program U: dsr_serve_start_user with U's hooks (its descriptor
+ * check by U::extent, its server kernel instantiated here; the table is
+ * dsr_serve_user_program<U>(), static, valid for the process). cfg->program
+ * must be U::kProgram. Requests then go through dsr_serve_submit /
+ * dsr_serve_poll / dsr_serve_stop like a built-in program's. */
+template <class U>
+const dsr_serve_program *dsr_serve_user_program() {
+  static_assert(U::kProgram >= DSR_PROG_USER, "user programs take ids >= DSR_PROG_USER");
+  static const dsr_serve_program prog = {U::kProgram, 0u, &dsr::UserServer<U>::validate,
+                                         &dsr::UserServer<U>::prepare,
+                                         &dsr::UserServer<U>::launch};
+  return &prog;
+}
+
+template <class U>
+int32_t dsr_serve_user_start(dsr_ctx *ctx, const dsr_serve_cfg *cfg, void *workspace_dev,
+                             uint64_t workspace_bytes) {
+  return dsr_serve_start_user(ctx, cfg, workspace_dev, workspace_bytes,
+                              dsr_serve_user_program<U>());
 }
 
 #endif /* DSR_DEVICE_CUH_ */

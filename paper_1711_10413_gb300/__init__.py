@@ -55,6 +55,18 @@ class dsr_batch_tuning(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
+class dsr_serve_program(ctypes.Structure):
+    """Hooks of a user-written program's server (filled in by the device
+    API's dsr_serve_user_start in the program's own library)."""
+    _fields_ = [("program", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("validate", ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_uint64,
+                                              ctypes.c_uint64, ctypes.c_uint64)),
+                ("prepare", ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32,
+                                             ctypes.POINTER(ctypes.c_int32))),
+                ("launch", ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_uint32,
+                                            ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p))]
+
+
 class dsr_serve_cfg(ctypes.Structure):
     _fields_ = [("program", ctypes.c_uint32), ("threads", ctypes.c_uint32),
                 ("slab_bytes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
@@ -166,6 +178,7 @@ def _declare(L):
                                      P(dsr_batch_plan)]),
         "dsr_serve_workspace_bytes": (_u64, [_u32]),
         "dsr_serve_start": (_i32, [_vp, P(dsr_serve_cfg), _vp, _u64]),
+        "dsr_serve_start_user": (_i32, [_vp, P(dsr_serve_cfg), _vp, _u64, P(dsr_serve_program)]),
         "dsr_serve_submit": (_i32, [_vp, P(dsr_region_desc), P(_u64)]),
         "dsr_serve_poll": (_i32, [_vp, _u64, P(_i32)]),
         "dsr_serve_stop": (_i32, [_vp]),
@@ -207,7 +220,7 @@ def exported_symbols():
             "dsr_batch_static_errors", "dsr_batch_abort", "dsr_batch_progress",
             "dsr_report_error", "dsr_user_plain_config",
             "dsr_batch_prepare",
-            "dsr_serve_workspace_bytes", "dsr_serve_start",
+            "dsr_serve_workspace_bytes", "dsr_serve_start", "dsr_serve_start_user",
             "dsr_serve_submit", "dsr_serve_poll", "dsr_serve_stop", "dsr_serve_stats",
             "dsr_serve_bench", "dsr_launch_bench", "dsr_check_bounded_wait",
             "dsr_check_stack", "dsr_probe_smem_bandwidth"]
@@ -511,11 +524,25 @@ def dsr_serve_workspace_bytes(capacity: int) -> int:
 def dsr_serve_start(ctx: int, program: int, images, out, status, workspace, threads: int = 128,
                     slab_bytes: int = 16384, capacity: int = 4096, ctas_per_sm: int = 0,
                     idle_timeout_ns: int = 0) -> None:
-    cfg = dsr_serve_cfg(program, threads, slab_bytes, ctas_per_sm, capacity, 0, idle_timeout_ns,
-                        _ptr(images), _nbytes(images) if images is not None else 0, _ptr(out),
-                        _nbytes(out), _ptr(status), _nbytes(status) // 32)
+    cfg = serve_cfg(program, images, out, status, threads, slab_bytes, capacity, ctas_per_sm,
+                    idle_timeout_ns)
     _check(lib().dsr_serve_start(ctx, ctypes.byref(cfg), _ptr(workspace), _nbytes(workspace)),
            ctx)
+
+
+def serve_cfg(program: int, images, out, status, threads: int = 128, slab_bytes: int = 16384,
+              capacity: int = 4096, ctas_per_sm: int = 0, idle_timeout_ns: int = 0):
+    """A dsr_serve_cfg over the given device buffers."""
+    return dsr_serve_cfg(program, threads, slab_bytes, ctas_per_sm, capacity, 0, idle_timeout_ns,
+                         _ptr(images), _nbytes(images) if images is not None else 0, _ptr(out),
+                         _nbytes(out), _ptr(status), _nbytes(status) // 32)
+
+
+def dsr_serve_start_user(ctx: int, cfg, workspace, prog) -> None:
+    """Serve a user-written program: `prog` a dsr_serve_program (its hooks
+    from the program's library)."""
+    _check(lib().dsr_serve_start_user(ctx, ctypes.byref(cfg), _ptr(workspace),
+                                      _nbytes(workspace), ctypes.byref(prog)), ctx)
 
 
 def dsr_serve_submit(ctx: int, region):

@@ -185,7 +185,8 @@ def test_user_program_library_builds_and_exports(L):
     dsr_build.build_user([src], out)
     U = ctypes.CDLL(out)
     for name in ("user_paper_scalars", "user_hetero"):
-        for suffix in ("_launch", "_launch_batch", "_program"):
+        for suffix in ("_launch", "_launch_batch", "_serve_start", "_serve_program",
+                       "_program"):
             assert hasattr(U, name + suffix)
     U.user_hetero_program.restype = ctypes.c_uint32
     assert U.user_hetero_program() == dsr.DSR_PROG_USER + 6
@@ -195,6 +196,43 @@ def test_user_program_library_builds_and_exports(L):
     r.program = 200   # neither built in nor in the user range
     with pytest.raises(dsr.DsrError):
         dsr.dsr_region_extent(r)
+
+
+def test_user_server_hooks_check_descriptors(L):
+    """The hook table a user program's server hands the library: its id, and
+    a descriptor check (host code, run here) that passes well-formed
+    requests inside the server's buffers and refuses the rest; the start
+    call refuses a missing ctx or table without touching a GPU."""
+    import ctypes
+    src = os.path.join(ROOT, "tests", "user_program", "user_programs.cu")
+    out = os.path.join(ROOT, "tests", "user_program", "libuser_programs.so")
+    dsr_build.build_user([src], out)
+    U = ctypes.CDLL(out)
+    U.user_hetero_serve_program.restype = ctypes.POINTER(dsr.dsr_serve_program)
+    prog = U.user_hetero_serve_program().contents
+    assert prog.program == dsr.DSR_PROG_USER + 6 and prog.reserved == 0
+    assert prog.validate and prog.prepare and prog.launch
+    work = wl.hetero(n_instances=6, max_teams=4, max_frame=2048, seed=4)
+    ib = work.images.nbytes
+    ob = work.out_bytes
+    ns = work.n_status
+    for r in work.regions:
+        r.program = dsr.DSR_PROG_USER + 6
+        d = dsr.pack_desc(r)
+        assert prog.validate(ctypes.addressof(d), ib, ob, ns) == dsr.DSR_OK
+        # outputs, images or statuses one short of what the region indexes
+        end_out = r.out_offset + 4 * r.teams * (r.width or max(r.threads - 32, 1))
+        assert prog.validate(ctypes.addressof(d), ib, end_out - 4, ns) == dsr.DSR_ERR_INVALID
+        assert prog.validate(ctypes.addressof(d), ib, ob, r.status_index + r.teams - 1) == \
+            dsr.DSR_ERR_INVALID
+        d.program = dsr.DSR_PROG_HETERO   # another program's descriptor
+        assert prog.validate(ctypes.addressof(d), ib, ob, ns) == dsr.DSR_ERR_INVALID
+    cfg = dsr.dsr_serve_cfg()
+    cfg.program = prog.program
+    assert dsr.lib().dsr_serve_start_user(None, ctypes.byref(cfg), None, 0,
+                                          ctypes.byref(prog)) == dsr.DSR_ERR_INVALID
+    assert dsr.lib().dsr_serve_start_user(None, ctypes.byref(cfg), None, 0, None) == \
+        dsr.DSR_ERR_INVALID
 
 
 def test_batch_abort_and_progress_refuse_without_ctx(L):

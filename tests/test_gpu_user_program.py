@@ -242,3 +242,103 @@ def test_user_plain_refusals(user):
     cfg = dsr.dsr_user_plain_config(rt.ctx, uw.regions[0], 0, 16, 0, out.numel() * 4,
                                     status.numel() // 8, out, status)
     assert cfg["slab_bytes"] == 4096 and cfg["ctrl_bytes"] == 384
+
+
+def _serve_user(L, rt, name, work, threads, slab, capacity=64):
+    """Every region of `work` (naming the user program) through a server of
+    <name>'s program started with dsr_serve_user_start; (output, statuses,
+    completion statuses)."""
+    import time
+    import paper_1711_10413_gb300 as dsr
+    torch = rt.torch
+    images, out, status = rt.device_buffers(work)
+    ws = torch.empty(dsr.dsr_serve_workspace_bytes(capacity), dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    start = getattr(L, name + "_serve_start")
+    start.restype = ctypes.c_int32
+    start.argtypes = [ctypes.c_void_p, ctypes.POINTER(dsr.dsr_serve_cfg), ctypes.c_void_p,
+                      ctypes.c_uint64]
+    cfg = dsr.serve_cfg(work.regions[0].program, images, out, status, threads, slab, capacity)
+    _check(start(rt.ctx, ctypes.byref(cfg), ws.data_ptr(), ws.numel()), rt)
+    done = {}
+    try:
+        tickets, pending, t0 = [], list(work.regions), time.time()
+        while pending:
+            assert time.time() - t0 < 30
+            tk = dsr.dsr_serve_submit(rt.ctx, pending[0])
+            if tk is None:      # admission waits for completions
+                dsr.dsr_serve_poll(rt.ctx, 1 << 62)
+                continue
+            tickets.append(tk)
+            pending.pop(0)
+        left = set(tickets)
+        while left:
+            assert time.time() - t0 < 30, "requests did not complete"
+            for tk in list(left):
+                st = dsr.dsr_serve_poll(rt.ctx, tk)
+                if st != dsr.DSR_PENDING:
+                    done[tk] = st
+                    left.discard(tk)
+    finally:
+        dsr.dsr_serve_stop(rt.ctx)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), status.cpu().numpy().view(dsr.TEAM_STATUS_DTYPE), done
+
+
+@pytest.mark.parametrize("threads,slab", [(128, 8192), (256, 16384)])
+def test_user_hetero_served(user, threads, slab):
+    """The user-written hetero program served by the library's request loop
+    (dsr_serve_user_start: the server kernel instantiated in the program's
+    own library), many requests in flight at once: every output and team
+    record equals the oracle's."""
+    import paper_1711_10413_gb300 as dsr
+    L, rt = user
+    work = wl.hetero(n_instances=120, max_teams=24, max_frame=16384, seed=17)
+    uw = _as_user(work, L.user_hetero_program())
+    rt.configure(16384, 3 * 32768, 4096)
+    g, gs, done = _serve_user(L, rt, "user_hetero", uw, threads, slab)
+    assert len(done) == len(uw.regions) and all(v == dsr.DSR_OK for v in done.values())
+    r, rs = oracle.run_workload(work, slab_bytes=slab, overflow_bytes=3 * 32768)
+    assert np.array_equal(g[: r.size], r)
+    for f in ("status", "depth_final", "hwm_bytes", "spill_bytes", "chk"):
+        assert np.array_equal(gs[f], rs[f]), f
+    stats = dsr.dsr_serve_stats(rt.ctx)
+    assert stats["errors"] == 0
+
+
+def test_user_serve_refusals(user):
+    """Host-side refusals with a user program's server: a built-in program's
+    descriptor, and a request indexing past the outputs (nothing runs for
+    either); the built-in start refuses a user id."""
+    import paper_1711_10413_gb300 as dsr
+    L, rt = user
+    torch = rt.torch
+    work = wl.hetero(n_instances=3, max_teams=4, max_frame=1024, seed=8)
+    uw = _as_user(work, L.user_hetero_program())
+    rt.configure(16384, 3 * 32768, 4096)
+    images, out, status = rt.device_buffers(uw)
+    ws = torch.empty(dsr.dsr_serve_workspace_bytes(16), dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    with pytest.raises(dsr.DsrError) as ei:
+        dsr.dsr_serve_start(rt.ctx, uw.regions[0].program, images, out, status, ws,
+                            capacity=16)
+    assert "dsr_serve_start_user" in str(ei.value)
+    L.user_hetero_serve_start.restype = ctypes.c_int32
+    L.user_hetero_serve_start.argtypes = [ctypes.c_void_p, ctypes.POINTER(dsr.dsr_serve_cfg),
+                                          ctypes.c_void_p, ctypes.c_uint64]
+    cfg = dsr.serve_cfg(uw.regions[0].program, images, out, status, 128, 8192, 16)
+    _check(L.user_hetero_serve_start(rt.ctx, ctypes.byref(cfg), ws.data_ptr(), ws.numel()), rt)
+    try:
+        bad = copy.copy(work.regions[0])  # the built-in program's id
+        with pytest.raises(dsr.DsrError):
+            dsr.dsr_serve_submit(rt.ctx, bad)
+        far = copy.copy(uw.regions[0])
+        far.out_offset = out.numel() * 4   # past the outputs
+        with pytest.raises(dsr.DsrError) as ei:
+            dsr.dsr_serve_submit(rt.ctx, far)
+        assert "refused" in str(ei.value)
+        tk = dsr.dsr_serve_submit(rt.ctx, uw.regions[1])
+        assert tk is not None
+    finally:
+        dsr.dsr_serve_stop(rt.ctx)
+    assert dsr.dsr_serve_stats(rt.ctx)["completed"] == 1

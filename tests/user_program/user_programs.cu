@@ -182,6 +182,13 @@ static_assert(!dsr::has_prefetch<dsr::UserProgram<UserPaperScalars>>::value, "no
                                        out_bytes, status, n_status, ws, ws_bytes, tuning,      \
                                        stream);                                                \
   }                                                                                            \
+  extern "C" int32_t name##_serve_start(dsr_ctx *ctx, const dsr_serve_cfg *cfg, void *ws,      \
+                                        uint64_t ws_bytes) {                                   \
+    return dsr_serve_user_start<Prog>(ctx, cfg, ws, ws_bytes);                                 \
+  }                                                                                            \
+  extern "C" const dsr_serve_program *name##_serve_program(void) {                             \
+    return dsr_serve_user_program<Prog>();                                                     \
+  }                                                                                            \
   extern "C" uint32_t name##_program(void) { return Prog::kProgram; }
 
 USER_ENTRY(user_paper_scalars, UserPaperScalars)

@@ -53,8 +53,9 @@
  * programs run.
  *
  * Execution model.
- *  - master() runs on the 32 lanes of the team's master warp together (the
- *    last warp of the CTA; Sec. 4 reserves it for the master thread). Its
+ *  - master() runs on the 32 lanes of the team's master warp together (a
+ *    warp set aside for the master thread as in Sec. 4, the CTA's last
+ *    warp). Its
  *    control flow must be the same in all 32 lanes, and every dsr_* call on
  *    the master side is made by all 32 lanes at once. A statement that the
  *    paper's single master thread runs goes inside `if (dsr_is_master())`,

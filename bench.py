@@ -454,6 +454,35 @@ def measure_sweep(dsr, torch, device, flush, hbm_gbs, sizes=None):
 FORMS = ("sweep", "scalars", "batched", "served", "workers")
 
 
+def measure_host_link(torch, nbytes=16 << 20, reps=10):
+    """Copy bandwidth of the host link, each direction alone: 16 MiB between
+    pinned host memory and the device by cudaMemcpyAsync (torch's
+    non-blocking copy), CUDA events on the copying stream, best of three
+    rounds after a warm-up. The host-buffer path can move its bytes no
+    faster, so it bounds the e2e figure."""
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    s = torch.cuda.Stream()
+    res = {}
+    for name, dst, src in (("d2h_gbs", h, d), ("h2d_gbs", d, h)):
+        best = None
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                dst.copy_(src, non_blocking=True)
+            for _ in range(3):
+                a = torch.cuda.Event(enable_timing=True)
+                z = torch.cuda.Event(enable_timing=True)
+                a.record(s)
+                for _ in range(reps):
+                    dst.copy_(src, non_blocking=True)
+                z.record(s)
+                z.synchronize()
+                ms = a.elapsed_time(z)
+                best = ms if best is None else min(best, ms)
+        res[name] = nbytes * reps / (best * 1e-3) / 1e9
+    return res
+
+
 def measure_workers(dsr, torch, device, flush, sm_count):
     """Worker-level sharing: 1024 teams x 256 threads, each of the 224
     workers pushes a 256-byte frame on its warp's stack and runs a nested
@@ -910,6 +939,8 @@ def main():
         e2e_step()
     torch.cuda.synchronize()
     e2e_serial_s = shard.max_over_ranks((time.perf_counter() - t1) / args.steps, dist)
+    link = measure_host_link(torch)
+    e2e_bound = regions_done * link["d2h_gbs"] * 1e9 / (ob + 32 * region.teams)
 
     # the other launch forms (every rank takes part: with several ranks the
     # batched and served forms run on each rank's share)
@@ -947,7 +978,11 @@ def main():
                  d2h_bytes_per_step=int(ob + 32 * region.teams),
                  how="dsr_enqueue_region_host, steps alternating over two streams",
                  bad_team_status=e2e_bad[0], output_agrees=e2e_agree,
-                 one_step_at_a_time=regions_done / e2e_serial_s),
+                 one_step_at_a_time=regions_done / e2e_serial_s,
+                 link=dict(link, bound_regions_per_s=e2e_bound,
+                           frac=(regions_done / e2e_s) / e2e_bound,
+                           how="each rank's step download at the measured "
+                               "device-to-host copy bandwidth (16 MiB, pinned, alone)")),
         gpu_launches=args.steps,
         bracket_ms_per_step=1000.0 * bracket_s / args.steps,
         bad_team_status=bad_status,

@@ -824,13 +824,26 @@ def main():
         (images.clone(), torch.empty_like(out), torch.zeros_like(status))
         for _ in range(n_sets - 1)]
 
-    def step(i=0):
+    def step(i=0, s=None):
         im, o, st = sets[i % n_sets]
-        dsr.dsr_launch_region(rt.ctx, region, im, o, st, stream)
+        dsr.dsr_launch_region(rt.ctx, region, im, o, st, stream if s is None else s)
 
     warmup_launches = max(args.warmup, n_sets)  # every set used once before timing
     for i in range(warmup_launches):
         step(i)
+    torch.cuda.synchronize()
+
+    # The timed steps are the same K launches (set i mod n_sets for step i),
+    # issued by replaying a CUDA graph captured from them: consecutive
+    # launches keep their programmatic dependence as graph edges, and the GPU
+    # takes the K kernel nodes without a host call each. Issued one call at a
+    # time they are timed as well (direct_launches).
+    cap = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=cap):
+        for i in range(args.steps):
+            step(i, cap)
+    graph.replay()  # untimed: one more pass over every set
     torch.cuda.synchronize()
 
     t_start = torch.cuda.Event(enable_timing=True)
@@ -844,18 +857,30 @@ def main():
     # hold the stream for a moment so the host queues every step before the
     # GPU reaches it: the events then time the GPU alone, never a GPU that
     # waits for the host to launch the next kernel
-    torch.cuda._sleep(int(2.1e9 * (2e-3 + 30e-6 * args.steps)))
+    torch.cuda._sleep(int(2.1e9 * 2e-3))
     t_start.record(stream)
-    for i in range(args.steps):
-        step(i)
+    graph.replay()
     t_stop.record(stream)
     torch.cuda.synchronize()
     bracket_s = time.perf_counter() - t0
     if dist:
         dist.barrier()
+    torch.cuda.synchronize()
+    torch.cuda._sleep(int(2.1e9 * (2e-3 + 30e-6 * args.steps)))
+    d_start = torch.cuda.Event(enable_timing=True)
+    d_stop = torch.cuda.Event(enable_timing=True)
+    d_start.record(stream)
+    for i in range(args.steps):
+        step(i)
+    d_stop.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     clk = clocks.stop()
     ms_step = t_start.elapsed_time(t_stop) / args.steps
     ms_step = shard.max_over_ranks(ms_step, dist)   # the slowest rank's step
+    ms_direct = shard.max_over_ranks(d_start.elapsed_time(d_stop) / args.steps, dist)
+    del graph
     regions_done = shard.sum_over_ranks(1.0, dist)  # one region per rank per step
 
     # every team of every set must have ended OK with its stack empty, and
@@ -987,6 +1012,11 @@ def main():
         bracket_ms_per_step=1000.0 * bracket_s / args.steps,
         bad_team_status=bad_status,
         sets_agree=sets_agree,
+        direct_launches=dict(
+            ms_per_step=ms_direct, regions_per_s=regions_done * 1000.0 / ms_direct,
+            frac=algo_bytes / (ms_direct * 1e-3) / 1e9 / peaks["hbm_gbs"],
+            how="the same K launches, one dsr_launch_region call each"),
+        issue="the K timed launches replayed from one CUDA graph captured from them",
         per_launch_flushed=dict(
             ms=ms_flushed, regions_per_s=regions_done * 1000.0 / ms_flushed,
             frac=algo_bytes / (ms_flushed * 1e-3) / 1e9 / peaks["hbm_gbs"],

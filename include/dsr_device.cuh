@@ -320,9 +320,13 @@ int32_t dsr_launch_user_region(dsr_ctx *ctx, const dsr_region_desc *d, const voi
   if (ib && !images_dev) return dsr_report_error(ctx, DSR_ERR_INVALID, "null images");
   const uint32_t block = d->threads > 32u ? d->threads : 64u;
   const dsr::PlainFn k = dsr::pick_plain<P>(block);
-  const uint32_t smem = cfg.ctrl_bytes + cfg.slab_bytes;
-  cudaError_t e = dsr::ensure_smem_limit(reinterpret_cast<const void *>(k), cfg.device, smem);
+  cudaError_t e = dsr::ensure_smem_limit(reinterpret_cast<const void *>(k), cfg.device,
+                                         cfg.ctrl_bytes + cfg.slab_bytes);
   if (e != cudaSuccess) return dsr_report_error(ctx, DSR_ERR_CUDA, cudaGetErrorString(e));
+  // at most ceil(teams / SMs) CTAs per SM, as the library's plain launch
+  const uint32_t smem = dsr::balanced_smem(reinterpret_cast<const void *>(k), block,
+                                           cfg.ctrl_bytes + cfg.slab_bytes, d->teams, cfg.device,
+                                           cfg.max_smem);
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;

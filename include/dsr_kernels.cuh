@@ -18,8 +18,12 @@
 //                                          uint64_t *out_bytes);
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstdint>
+#include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "dsr.h"
 #include "dsr_check.cuh"
@@ -111,6 +115,71 @@ __global__ void __launch_bounds__(MAXT, MINB)
 
 using PlainFn = void (*)(dsr_region_desc, const uint8_t *, uint8_t *, dsr_team_status *,
                          uint8_t *, uint64_t, uint32_t, uint64_t);
+
+// Balanced residency of a plain launch. A launch of T teams on N SMs needs
+// at most ceil(T / N) teams on any SM, but the block scheduler fills an SM
+// up to the kernel's occupancy (with programmatic dependent launch, the SMs
+// the previous grid frees first take the most), and the launch ends with
+// its fullest SM. Dynamic shared memory asked for beyond what the program
+// uses caps the CTAs an SM can hold, so the launch asks for the least that
+// leaves room for ceil(T / N) CTAs and no more. Returns the dynamic shared
+// memory to launch kernel k with: `base` (control block and slab) when the
+// teams are no more than the SMs, when ceil(T / N) CTAs per SM is already
+// the occupancy or beyond it, or when the occupancy calculator does not
+// confirm exactly the cap at the padded size (which it then also allows in
+// the kernel's attributes). Host code; results are kept per (kernel, block,
+// base, T, device).
+inline uint32_t balanced_smem(const void *k, uint32_t block, uint32_t base, uint32_t teams,
+                              int device, uint32_t max_dyn) {
+  struct Entry {
+    const void *k;
+    uint32_t block, base, teams;
+    int device;
+    uint32_t smem;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> cache;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    for (const Entry &x : cache)
+      if (x.k == k && x.block == block && x.base == base && x.teams == teams && x.device == device)
+        return x.smem;
+  }
+  uint32_t smem = base;
+  int sms = 0, per_sm_smem = 0, reserved = 0, occ = 0;
+  cudaFuncAttributes fa{};
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess &&
+      cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) ==
+          cudaSuccess &&
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device) ==
+          cudaSuccess &&
+      cudaFuncGetAttributes(&fa, k) == cudaSuccess && sms > 0 &&
+      teams > static_cast<uint32_t>(sms) &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, static_cast<int>(block), base) ==
+          cudaSuccess) {
+    const uint32_t cap = (teams + sms - 1u) / static_cast<uint32_t>(sms);
+    if (cap < static_cast<uint32_t>(occ)) {
+      // (cap + 1) CTAs of this footprint exceed the SM's shared memory
+      const int64_t want = static_cast<int64_t>(per_sm_smem) / (cap + 1) -
+                           static_cast<int64_t>(fa.sharedSizeBytes) - reserved + 1;
+      const uint32_t dyn = static_cast<uint32_t>((want + 15) & ~int64_t(15));
+      int occ2 = 0;
+      if (want > static_cast<int64_t>(base) && dyn <= max_dyn &&
+          (static_cast<int>(dyn) <= fa.maxDynamicSharedSizeBytes ||
+           cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(dyn)) == cudaSuccess) &&
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k, static_cast<int>(block), dyn) ==
+              cudaSuccess &&
+          occ2 == static_cast<int>(cap))
+        smem = dyn;
+    }
+  }
+  cudaGetLastError();  // a refused query leaves the launch at `base`
+  std::lock_guard<std::mutex> g(mu);
+  if (cache.size() >= 64) cache.erase(cache.begin());
+  cache.push_back({k, block, base, teams, device, smem});
+  return smem;
+}
 
 // The plain kernel instance for a CTA of `threads` threads. Programs whose
 // launches fill the GPU with many teams (P::kDense) are held to 32

@@ -215,7 +215,10 @@ extern "C" int32_t dsr_destroy(dsr_ctx *ctx) {
   return DSR_OK;
 }
 
-static int32_t set_smem_attr(dsr_ctx *ctx, uint32_t smem) {
+// Every plain kernel instance may take all the dynamic shared memory a CTA
+// can opt in to (less its own static shared memory), with the carveout
+// preferring shared memory to L1.
+static int32_t set_smem_attr(dsr_ctx *ctx) {
   static const uint32_t kThreads[] = {128, 256, 512, 1024};
   for (uint32_t p = DSR_PROG_PAPER_SCALARS; p <= DSR_PROG_WORKERS + 1; ++p)
     for (uint32_t t : kThreads) {
@@ -227,10 +230,13 @@ static int32_t set_smem_attr(dsr_ctx *ctx, uint32_t smem) {
       cudaFuncAttributes fa{};
       cudaError_t e = cudaFuncGetAttributes(&fa, k);
       if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "cudaFuncGetAttributes");
+      // the ceiling is all a CTA may take: a plain launch asks for its slab
+      // or, to balance residency, a padded size (balanced_smem), and a
+      // ceiling set to one slab would refuse another's
       const uint32_t room = static_cast<uint32_t>(ctx->max_smem_optin) -
                             static_cast<uint32_t>(fa.sharedSizeBytes);
       e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               static_cast<int>(smem < room ? smem : room));
+                               static_cast<int>(room));
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared);
@@ -278,7 +284,7 @@ extern "C" int32_t dsr_stack_init(dsr_ctx *ctx, uint32_t smem_slab_bytes,
                       (unsigned long long)pool_bytes, max_teams,
                       (unsigned long long)overflow_bytes_per_team);
   }
-  int32_t rc = set_smem_attr(ctx, kCtrlBytes + smem_slab_bytes);
+  int32_t rc = set_smem_attr(ctx);
   if (rc != DSR_OK) return rc;
   rc = dsr_ctx_stack_changed(ctx, kCtrlBytes + smem_slab_bytes);
   if (rc != DSR_OK) return rc;
@@ -311,7 +317,10 @@ int32_t dsr_launch_plain(dsr_ctx *ctx, const dsr_region_desc *d, const void *ima
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(d->teams);
   cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = kCtrlBytes + slab;
+  // at most ceil(teams / SMs) CTAs per SM when fewer than the occupancy
+  cfg.dynamicSmemBytes = balanced_smem(reinterpret_cast<const void *>(k), block,
+                                       kCtrlBytes + slab, d->teams, ctx->device,
+                                       static_cast<uint32_t>(ctx->max_smem_optin));
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
@@ -417,9 +426,14 @@ extern "C" int32_t dsr_region_occupancy(dsr_ctx *ctx, const dsr_region_desc *d,
   int per_sm = 0;
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k);
+  // resident CTAs of the launch as made: the balanced dynamic shared memory
+  const uint32_t launch_smem =
+      e == cudaSuccess ? balanced_smem(k, block, smem, d->teams, ctx->device,
+                                       static_cast<uint32_t>(ctx->max_smem_optin))
+                       : smem;
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, static_cast<int>(block),
-                                                      static_cast<size_t>(smem));
+                                                      static_cast<size_t>(launch_smem));
   if (e != cudaSuccess) return dsr_cuda_fail(ctx, e, "occupancy query");
   const uint64_t spill = dsr::spill_bytes(*d, slab);
   out->threads = block;

@@ -217,6 +217,28 @@ def test_region_occupancy_matches_model_limits(rt):
     assert occ["spill_bytes"] == 196608 and occ["smem_per_team"] == 384
 
 
+def test_balanced_residency_caps_ctas_per_sm(rt):
+    """A plain launch of more teams than SMs holds at most ceil(teams / SMs)
+    of them on an SM (its dynamic shared memory padded past what the
+    program uses), when that is below the kernel's occupancy; the results
+    are the oracle's either way. Up to the SM count, and at or above the
+    occupancy, nothing changes."""
+    probe = wl.nested(teams=8, threads=256, depth=3).regions[0]
+    _configure(rt, 3264)
+    occ8 = rt.occupancy(probe)
+    sms, full = occ8["sm_count"], occ8["ctas_per_sm"]
+    assert full == 8 and occ8["smem_per_team"] == 384 + 3264
+    for teams in (sms + 1, 2 * sms + 1, 5 * sms, 7 * sms, 9 * sms):
+        work = wl.nested(teams=teams, threads=256, depth=3, elems_per_team=256, seed=teams)
+        occ = rt.occupancy(work.regions[0])
+        cap = -(-teams // sms)
+        assert occ["ctas_per_sm"] == (cap if cap < full else full), (teams, occ)
+        assert occ["smem_per_team"] == 384 + 3264   # what the program uses
+        g, gs, r, rs = _run_both(rt, work, slab=3264)
+        assert _same_out(g, r)
+        _assert_status_equal(gs, rs)
+
+
 # ---------------------------------------------------------------------------
 # Worker-level sharing (Sec. 7): per-warp stacks, nested regions on warps
 # ---------------------------------------------------------------------------

@@ -236,8 +236,10 @@ int32_t dsr_footprint_model(const dsr_region_desc *d, uint32_t slab_bytes, uint3
 typedef struct dsr_occupancy {
   uint32_t threads;         /* CTA threads of the launch (one extra warp when threads == 32) */
   uint32_t regs_per_thread; /* registers of the kernel the launch runs */
-  uint32_t smem_per_team;   /* dynamic shared memory per CTA: control block + slab */
-  uint32_t ctas_per_sm;     /* resident teams per SM (the CUDA occupancy calculator) */
+  uint32_t smem_per_team;   /* shared memory a team uses: control block + slab */
+  uint32_t ctas_per_sm;     /* resident teams per SM as launched (the CUDA occupancy
+                               calculator at the launch's dynamic shared memory, which
+                               balanced residency may pad: see dsr_launch_region) */
   uint32_t sm_count;        /* SMs of the device */
   uint32_t spill_bytes;     /* bytes per team its frames put in the overflow slab */
 } dsr_occupancy;
@@ -260,8 +262,12 @@ int32_t dsr_region_occupancy(dsr_ctx *ctx, const dsr_region_desc *d, dsr_occupan
  * programmatic stream serialisation: its CTAs may be placed while the kernel
  * before it in the stream drains, but none of its threads touches global
  * memory before that kernel has completed, so stream order holds for every
- * buffer. Errors: DSR_ERR_INVALID, DSR_ERR_BUDGET, DSR_ERR_CUDA (launch
- * failure). */
+ * buffer. Balanced residency: when d->teams exceeds the SM count and
+ * ceil(teams / SMs) CTAs per SM is below the kernel's occupancy, the launch
+ * asks for enough dynamic shared memory (beyond the control block and slab
+ * it uses) that no SM holds more than ceil(teams / SMs) of its teams, so
+ * that no SM ends the launch later for holding more than its share.
+ * Errors: DSR_ERR_INVALID, DSR_ERR_BUDGET, DSR_ERR_CUDA (launch failure). */
 int32_t dsr_launch_region(dsr_ctx *ctx, const dsr_region_desc *d, const void *images_dev,
                           uint64_t image_bytes, void *out_dev, uint64_t out_bytes,
                           dsr_team_status *status_dev, uint64_t n_status, void *stream);

@@ -616,10 +616,25 @@ struct ProgHetero {
       const uint32_t L = c->frames[m].bytes / 4u, nv = L / 4u, tag = (m + 1u) << 24;
       const uint4 *f4 = reinterpret_cast<const uint4 *>(f);
       uint32_t r = (4u * first) % n;  // (4 i) mod n for this worker's vector i
-      for (uint32_t i = first; i < nv; i += W) {
-        add_vec(acc, f4[i], 4u * i, tag, r, n);
-        r += step;
-        r = r >= n ? r - n : r;
+      if ((n & 3u) == 0) {
+        // r is then a multiple of 4 below n: its vector's 4 outputs are
+        // r .. r + 3, none past n
+        for (uint32_t i = first; i < nv; i += W) {
+          const uint4 x = f4[i];
+          const uint32_t tw = tag ^ (4u * i);  // 4i + c == 4i ^ c for c < 4
+          atomicAdd(acc + r, mix32(x.x ^ tw));
+          atomicAdd(acc + r + 1u, mix32(x.y ^ tw ^ 1u));
+          atomicAdd(acc + r + 2u, mix32(x.z ^ tw ^ 2u));
+          atomicAdd(acc + r + 3u, mix32(x.w ^ tw ^ 3u));
+          r += step;
+          r = r >= n ? r - n : r;
+        }
+      } else {
+        for (uint32_t i = first; i < nv; i += W) {
+          add_vec(acc, f4[i], 4u * i, tag, r, n);
+          r += step;
+          r = r >= n ? r - n : r;
+        }
       }
       for (uint32_t w = 4u * nv + first; w < L; w += W) atomicAdd(acc + w % n, mix32(f[w] ^ tag ^ w));
     }

@@ -834,16 +834,14 @@ def main():
     torch.cuda.synchronize()
 
     # The timed steps are the same K launches (set i mod n_sets for step i),
-    # issued by replaying a CUDA graph captured from them: consecutive
-    # launches keep their programmatic dependence as graph edges, and the GPU
-    # takes the K kernel nodes without a host call each. Issued one call at a
-    # time they are timed as well (direct_launches).
-    cap = torch.cuda.Stream()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=cap):
-        for i in range(args.steps):
-            step(i, cap)
-    graph.replay()  # untimed: one more pass over every set
+    # issued by replaying the library's launch graph of them
+    # (dsr_graph_capture_regions): consecutive launches keep their
+    # programmatic dependence as graph edges, and the GPU takes the K kernel
+    # nodes without a host call each. Issued one call at a time they are timed
+    # as well (direct_launches).
+    graph = dsr.dsr_graph_capture_regions(rt.ctx, [region] * args.steps,
+                                          [sets[i % n_sets] for i in range(args.steps)])
+    dsr.dsr_graph_launch(rt.ctx, graph, stream)  # untimed: one more pass over every set
     torch.cuda.synchronize()
 
     t_start = torch.cuda.Event(enable_timing=True)
@@ -859,7 +857,7 @@ def main():
     # waits for the host to launch the next kernel
     torch.cuda._sleep(int(2.1e9 * 2e-3))
     t_start.record(stream)
-    graph.replay()
+    dsr.dsr_graph_launch(rt.ctx, graph, stream)
     t_stop.record(stream)
     torch.cuda.synchronize()
     bracket_s = time.perf_counter() - t0
@@ -880,7 +878,7 @@ def main():
     ms_step = t_start.elapsed_time(t_stop) / args.steps
     ms_step = shard.max_over_ranks(ms_step, dist)   # the slowest rank's step
     ms_direct = shard.max_over_ranks(d_start.elapsed_time(d_stop) / args.steps, dist)
-    del graph
+    dsr.dsr_graph_destroy(graph)
     regions_done = shard.sum_over_ranks(1.0, dist)  # one region per rank per step
 
     # every team of every set must have ended OK with its stack empty, and
@@ -1016,7 +1014,8 @@ def main():
             ms_per_step=ms_direct, regions_per_s=regions_done * 1000.0 / ms_direct,
             frac=algo_bytes / (ms_direct * 1e-3) / 1e9 / peaks["hbm_gbs"],
             how="the same K launches, one dsr_launch_region call each"),
-        issue="the K timed launches replayed from one CUDA graph captured from them",
+        issue="the K timed launches replayed from one launch graph "
+              "(dsr_graph_capture_regions, dsr_graph_launch)",
         per_launch_flushed=dict(
             ms=ms_flushed, regions_per_s=regions_done * 1000.0 / ms_flushed,
             frac=algo_bytes / (ms_flushed * 1e-3) / 1e9 / peaks["hbm_gbs"],

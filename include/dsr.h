@@ -295,6 +295,45 @@ int32_t dsr_enqueue_region_host(dsr_ctx *ctx, const dsr_region_desc *d, const vo
                                 dsr_team_status *status_host, void *images_dev, void *out_dev,
                                 dsr_team_status *status_dev, void *stream);
 
+/* ---- launch graphs: repeated plain launches without a host call each ---- */
+
+/* The buffers one region's descriptor offsets index (device memory,
+ * caller-owned), as dsr_launch_region takes them. */
+typedef struct dsr_region_buffers {
+  const void *images_dev;
+  uint64_t image_bytes;
+  void *out_dev;
+  uint64_t out_bytes;
+  dsr_team_status *status_dev;
+  uint64_t n_status;
+} dsr_region_buffers;
+
+/* An instantiated CUDA graph of plain region launches. */
+typedef struct dsr_graph dsr_graph;
+
+/* Capture n plain launches into a CUDA graph: launch i runs descs[i] on
+ * bufs[i], checked as dsr_launch_region checks it, with the same
+ * programmatic stream serialisation, so each launch of the graph depends on
+ * the one before it as consecutive launches on a stream do (its CTAs may be
+ * placed while that one drains; none touches global memory before it has
+ * completed). Nothing runs until dsr_graph_launch. *out receives the graph
+ * (caller-owned, dsr_graph_destroy). The graph keeps the ctx's stack
+ * configuration of the capture (slab, overflow pool): a later dsr_stack_init
+ * on ctx makes its replays refuse. Errors: those of dsr_launch_region for a
+ * launch it would refuse (with the launch's index in the message; nothing
+ * is kept), DSR_ERR_INVALID (null argument, n == 0), DSR_ERR_CUDA. */
+int32_t dsr_graph_capture_regions(dsr_ctx *ctx, const dsr_region_desc *descs,
+                                  const dsr_region_buffers *bufs, uint32_t n, dsr_graph **out);
+
+/* Replay the graph's launches, in order, on `stream` (one host call for all
+ * of them). Asynchronous. Errors: DSR_ERR_INVALID (null argument, another
+ * ctx's or device's graph, or the stack configuration changed since the
+ * capture), DSR_ERR_CUDA. */
+int32_t dsr_graph_launch(dsr_ctx *ctx, dsr_graph *g, void *stream);
+
+/* Free the graph; its replays must have completed. NULL is accepted. */
+int32_t dsr_graph_destroy(dsr_graph *g);
+
 /* ---- batched launch: many instances, one persistent kernel -------------- */
 
 /* CTA shape of the persistent kernel. Teams of any width run on it: a region

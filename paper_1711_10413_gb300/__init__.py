@@ -55,6 +55,12 @@ class dsr_batch_tuning(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
+class dsr_region_buffers(ctypes.Structure):
+    _fields_ = [("images_dev", ctypes.c_void_p), ("image_bytes", ctypes.c_uint64),
+                ("out_dev", ctypes.c_void_p), ("out_bytes", ctypes.c_uint64),
+                ("status_dev", ctypes.c_void_p), ("n_status", ctypes.c_uint64)]
+
+
 class dsr_serve_program(ctypes.Structure):
     """Hooks of a user-written program's server (filled in by the device
     API's dsr_serve_user_start in the program's own library)."""
@@ -177,6 +183,10 @@ def _declare(L):
                                      _u64, _vp, _u64, _u32, _u32, _u32, _vp,
                                      P(dsr_batch_plan)]),
         "dsr_serve_workspace_bytes": (_u64, [_u32]),
+        "dsr_graph_capture_regions": (_i32, [_vp, P(dsr_region_desc), P(dsr_region_buffers), _u32,
+                                              P(_vp)]),
+        "dsr_graph_launch": (_i32, [_vp, _vp, _vp]),
+        "dsr_graph_destroy": (_i32, [_vp]),
         "dsr_serve_start": (_i32, [_vp, P(dsr_serve_cfg), _vp, _u64]),
         "dsr_serve_start_user": (_i32, [_vp, P(dsr_serve_cfg), _vp, _u64, P(dsr_serve_program)]),
         "dsr_serve_submit": (_i32, [_vp, P(dsr_region_desc), P(_u64)]),
@@ -220,6 +230,7 @@ def exported_symbols():
             "dsr_batch_static_errors", "dsr_batch_abort", "dsr_batch_progress",
             "dsr_report_error", "dsr_user_plain_config",
             "dsr_batch_prepare",
+            "dsr_graph_capture_regions", "dsr_graph_launch", "dsr_graph_destroy",
             "dsr_serve_workspace_bytes", "dsr_serve_start", "dsr_serve_start_user",
             "dsr_serve_submit", "dsr_serve_poll", "dsr_serve_stop", "dsr_serve_stats",
             "dsr_serve_bench", "dsr_launch_bench", "dsr_check_bounded_wait",
@@ -356,6 +367,29 @@ def dsr_launch_region(ctx: int, region, images, out, status, stream=None) -> Non
                                    _nbytes(images) if images is not None else 0, _ptr(out),
                                    _nbytes(out), _ptr(status), _nbytes(status) // 32,
                                    _stream(stream)), ctx)
+
+
+def dsr_graph_capture_regions(ctx: int, regions, buffers) -> int:
+    """A launch graph of len(regions) plain launches, region i on buffers[i]
+    = (images, out, status) device tensors; returns the graph handle
+    (dsr_graph_destroy frees it)."""
+    n = len(regions)
+    descs = (dsr_region_desc * n)(*[pack_desc(r) for r in regions])
+    bufs = (dsr_region_buffers * n)()
+    for i, (images, out, status) in enumerate(buffers):
+        bufs[i] = dsr_region_buffers(_ptr(images), _nbytes(images) if images is not None else 0,
+                                     _ptr(out), _nbytes(out), _ptr(status), _nbytes(status) // 32)
+    g = ctypes.c_void_p()
+    _check(lib().dsr_graph_capture_regions(ctx, descs, bufs, n, ctypes.byref(g)), ctx)
+    return g.value
+
+
+def dsr_graph_launch(ctx: int, graph: int, stream=None) -> None:
+    _check(lib().dsr_graph_launch(ctx, graph, _stream(stream)), ctx)
+
+
+def dsr_graph_destroy(graph: int) -> None:
+    lib().dsr_graph_destroy(graph)
 
 
 def dsr_run_region_host(ctx: int, region, images_host, image_bytes: int, out_host,

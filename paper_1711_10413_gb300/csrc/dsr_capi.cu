@@ -295,12 +295,20 @@ extern "C" int32_t dsr_stack_init(dsr_ctx *ctx, uint32_t smem_slab_bytes,
   ctx->pool = static_cast<uint8_t *>(overflow_pool_dev);
   ctx->pool_bytes = pool_bytes;
   ctx->stack_ready = true;
+  ++ctx->stack_gen;
   return DSR_OK;
 }
 
 // ---------------------------------------------------------------------------
 // Plain launch
 // ---------------------------------------------------------------------------
+uint32_t dsr_plain_launch_smem(dsr_ctx *ctx, const dsr_region_desc *d) {
+  const uint32_t block = d->threads > 32u ? d->threads : 64u;
+  const void *k = reinterpret_cast<const void *>(plain_kernel_for(d->program, block, d->param));
+  return balanced_smem(k, block, kCtrlBytes + dsr_plain_slab(ctx, d), d->teams, ctx->device,
+                       static_cast<uint32_t>(ctx->max_smem_optin));
+}
+
 int32_t dsr_launch_plain(dsr_ctx *ctx, const dsr_region_desc *d, const void *images_dev,
                          void *out_dev, dsr_team_status *status_dev, cudaStream_t s) {
   // a team without workers gets one worker warp (its region width is 1)
@@ -318,9 +326,7 @@ int32_t dsr_launch_plain(dsr_ctx *ctx, const dsr_region_desc *d, const void *ima
   cfg.gridDim = dim3(d->teams);
   cfg.blockDim = dim3(block);
   // at most ceil(teams / SMs) CTAs per SM when fewer than the occupancy
-  cfg.dynamicSmemBytes = balanced_smem(reinterpret_cast<const void *>(k), block,
-                                       kCtrlBytes + slab, d->teams, ctx->device,
-                                       static_cast<uint32_t>(ctx->max_smem_optin));
+  cfg.dynamicSmemBytes = dsr_plain_launch_smem(ctx, d);
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
@@ -395,11 +401,9 @@ extern "C" int32_t dsr_user_plain_config(dsr_ctx *ctx, const dsr_region_desc *d,
   return DSR_OK;
 }
 
-extern "C" int32_t dsr_launch_region(dsr_ctx *ctx, const dsr_region_desc *d,
-                                     const void *images_dev, uint64_t image_bytes,
-                                     void *out_dev, uint64_t out_bytes,
-                                     dsr_team_status *status_dev, uint64_t n_status,
-                                     void *stream) {
+int32_t dsr_check_region_launch(dsr_ctx *ctx, const dsr_region_desc *d, const void *images_dev,
+                                uint64_t image_bytes, const void *out_dev, uint64_t out_bytes,
+                                const void *status_dev, uint64_t n_status) {
   int32_t rc = check_launch(ctx, d, out_dev, status_dev);
   if (rc != DSR_OK) return rc;
   if ((rc = dsr_validate_region(d, image_bytes, out_bytes, n_status)) != DSR_OK)
@@ -407,6 +411,17 @@ extern "C" int32_t dsr_launch_region(dsr_ctx *ctx, const dsr_region_desc *d,
   uint64_t ib = 0;
   dsr_region_extent(d, &ib, nullptr, nullptr);
   if (ib && !images_dev) return dsr_fail(ctx, DSR_ERR_INVALID, "null images");
+  return DSR_OK;
+}
+
+extern "C" int32_t dsr_launch_region(dsr_ctx *ctx, const dsr_region_desc *d,
+                                     const void *images_dev, uint64_t image_bytes,
+                                     void *out_dev, uint64_t out_bytes,
+                                     dsr_team_status *status_dev, uint64_t n_status,
+                                     void *stream) {
+  int32_t rc = dsr_check_region_launch(ctx, d, images_dev, image_bytes, out_dev, out_bytes,
+                                       status_dev, n_status);
+  if (rc != DSR_OK) return rc;
   return dsr_launch_plain(ctx, d, images_dev, out_dev, status_dev,
                           static_cast<cudaStream_t>(stream));
 }

@@ -25,6 +25,7 @@ struct dsr_ctx {
   uint32_t max_teams = 0;
   uint8_t *pool = nullptr;
   uint64_t pool_bytes = 0;
+  uint64_t stack_gen = 0;   // dsr_stack_init calls that succeeded (launch graphs keep theirs)
   // launch forms
   dsr_batch_state *batch = nullptr;
   dsr_serve_state *serve = nullptr;
@@ -42,6 +43,13 @@ int32_t dsr_check_shape(const dsr_region_desc *d, const char **why);
 // Slab of a plain launch of *d: the configured slab, or with DSR_SLAB_AUTO
 // the region's footprint slab capped at what a CTA can hold.
 uint32_t dsr_plain_slab(const dsr_ctx *ctx, const dsr_region_desc *d);
+// The checks dsr_launch_region makes before it launches.
+int32_t dsr_check_region_launch(dsr_ctx *ctx, const dsr_region_desc *d, const void *images_dev,
+                                uint64_t image_bytes, const void *out_dev, uint64_t out_bytes,
+                                const void *status_dev, uint64_t n_status);
+// Dynamic shared memory of the plain launch of *d (slab, control block and
+// the balanced-residency padding); fills the host-side caches the launch reads.
+uint32_t dsr_plain_launch_smem(dsr_ctx *ctx, const dsr_region_desc *d);
 // The plain launch itself (arguments already checked).
 int32_t dsr_launch_plain(dsr_ctx *ctx, const dsr_region_desc *d, const void *images_dev,
                          void *out_dev, dsr_team_status *status_dev, cudaStream_t s);

@@ -242,3 +242,13 @@ def test_batch_abort_and_progress_refuse_without_ctx(L):
     t = ctypes.c_uint64()
     assert dsr.lib().dsr_batch_progress(None, None, ctypes.byref(t), None, None) == \
         dsr.DSR_ERR_INVALID
+
+
+def test_graph_calls_refuse_without_ctx(L):
+    """Host-side refusals of the launch-graph calls (no GPU touched)."""
+    import ctypes
+    g = ctypes.c_void_p()
+    assert dsr.lib().dsr_graph_capture_regions(None, None, None, 0, ctypes.byref(g)) == \
+        dsr.DSR_ERR_INVALID
+    assert dsr.lib().dsr_graph_launch(None, None, None) == dsr.DSR_ERR_INVALID
+    assert dsr.lib().dsr_graph_destroy(None) == dsr.DSR_OK

@@ -634,6 +634,13 @@ def measure_batched(dsr, torch, rt, flush, sm_count, instances=10000, tuning=Non
     # region's footprint instead of one 16 KiB slab for all
     rt.configure(dsr.DSR_SLAB_AUTO, 3 * 32768, 4096)
     ms_auto = shard.max_over_ranks(_event_ms(torch, lambda: rt.launch_regions(b), 2, flush), dist)
+    # ... and those launches replayed from one launch graph (no host call per
+    # instance): the strongest one-launch-per-region baseline
+    graph = dsr.dsr_graph_capture_regions(rt.ctx, work.regions,
+                                          [(b["images"], b["out"], b["status"])] * len(work.regions))
+    ms_graph = shard.max_over_ranks(
+        _event_ms(torch, lambda: dsr.dsr_graph_launch(rt.ctx, graph), 2, flush), dist)
+    dsr.dsr_graph_destroy(graph)
     rt.configure(16384, 3 * 32768, 4096)
     stack = shard.sum_over_ranks(hetero_stack_bytes(work.regions), dist)
     push_pop = shard.sum_over_ranks(sum(r.teams * r.depth for r in work.regions), dist)
@@ -647,8 +654,10 @@ def measure_batched(dsr, torch, rt, flush, sm_count, instances=10000, tuning=Non
                             batched_regions_per_s=instances / (ms_batch * 1e-3),
                             per_launch_regions_per_s=instances / (ms_plain * 1e-3),
                             per_launch_auto_slab_regions_per_s=instances / (ms_auto * 1e-3),
+                            per_launch_graph_regions_per_s=instances / (ms_graph * 1e-3),
                             batched_push_pop_per_s=push_pop / (ms_batch * 1e-3),
                             speedup=ms_plain / ms_batch,
+                            speedup_vs_graph=ms_graph / ms_batch,
                             stack_roofline=dict(bound="smem", stack_bytes=stack,
                                                 achieved=smem_gbs,
                                                 peak=world * smem_peak_gbs(sm_count),

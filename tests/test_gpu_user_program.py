@@ -342,3 +342,20 @@ def test_user_serve_refusals(user):
     finally:
         dsr.dsr_serve_stop(rt.ctx)
     assert dsr.dsr_serve_stats(rt.ctx)["completed"] == 1
+
+
+def test_user_plain_launch_with_more_teams_than_sms(user):
+    """A user program's plain launch of more teams than SMs goes through the
+    same balanced-residency padding as the library's (the launch template
+    asks for it): the results are the oracle's."""
+    import torch
+    L, rt = user
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for teams in (2 * sms + 1, 5 * sms):
+        work = wl.paper_scalars(9, teams=teams, threads=128, seed=teams)
+        uw = _as_user(work, L.user_paper_scalars_program())
+        rt.configure(4096, 0, 0)
+        g, gs = _plain(L, rt, "user_paper_scalars", uw)
+        r, rs = oracle.run_workload(work, slab_bytes=4096)
+        assert np.array_equal(g[: r.size], r)
+        _same_status(gs, rs)

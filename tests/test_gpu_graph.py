@@ -102,3 +102,32 @@ def test_graph_capture_refuses_and_replays_check_the_stack(rt):
             other.close()
     finally:
         dsr.dsr_graph_destroy(g)
+
+
+def test_graph_headline_full_size_on_rotating_sets(rt):
+    """The headline at full size (1024 teams x 256 threads, depth 3, 4096
+    elements per team) in the configuration bench.py times: a launch graph
+    of launches over rotating buffer sets, back to back, at most
+    ceil(1024 / SMs) teams per SM. Every set's output and team records equal
+    the oracle's."""
+    import paper_1711_10413_gb300 as dsr
+    torch = rt.torch
+    work = wl.nested(teams=1024, threads=256, depth=3, elems_per_team=4096)
+    rt.configure(3264, 0, 0)
+    sets = _sets(rt, work, 4)
+    order = [i % 4 for i in range(10)]
+    g = dsr.dsr_graph_capture_regions(rt.ctx, work.regions * len(order), [sets[i] for i in order])
+    try:
+        dsr.dsr_graph_launch(rt.ctx, g)
+        dsr.dsr_graph_launch(rt.ctx, g)
+        torch.cuda.synchronize()
+    finally:
+        dsr.dsr_graph_destroy(g)
+    occ = rt.occupancy(work.regions[0])
+    assert occ["ctas_per_sm"] == -(-1024 // occ["sm_count"])
+    r, rs = oracle.run_workload(work, slab_bytes=3264)
+    for _, o, st in sets:
+        assert np.array_equal(o.cpu().numpy(), r)
+        gs = st.cpu().numpy().view(dsr.TEAM_STATUS_DTYPE)
+        for f in ("status", "depth_final", "hwm_bytes", "spill_bytes", "chk"):
+            assert np.array_equal(gs[f], rs[f]), f

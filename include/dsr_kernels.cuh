@@ -225,16 +225,22 @@ static_assert(sizeof(WsHeader) == 128 + 8 * kBuckets + 128 * kGroups, "workspace
 // bytes: control block, slab, accumulator area.
 constexpr uint32_t batch_smem(uint32_t slab) { return kCtrlBytes + slab + kAccBytes; }
 
-// The persistent kernel's master warp pulls tasks in chunks of kGrab
-// consecutive tasks (consecutive teams of one instance share its descriptor
-// and images, which then hit in cache). 10,000 hetero instances on 128-thread
-// CTAs: 5.65 ms with chunks of 1, 5.51 with 2, 5.44 with 4, 5.76-5.88 with 8
-// and 6.7-7.0 with 16 (the last chunks leave CTAs idle at the batch's end).
-constexpr uint32_t kGrab = 4;
+// The persistent kernel's master warp pulls tasks in chunks of consecutive
+// tasks (consecutive teams of one instance share its descriptor and images,
+// which then hit in cache): chunks of 4 when every CTA has at least
+// kLongBatch tasks to take, else 2. The tasks run longest first, so a CTA
+// whose chunk holds several of the heaviest runs them in turn, and in a
+// short batch those first chunks set the batch's end. Hetero instances on
+// 128-thread CTAs (2,432 CTAs), chunks of 2 / 4: 10,000 instances (about 330
+// tasks per CTA) 5.51 / 5.44 ms; 2,000 (66 per CTA) 1.69-1.74 / 2.28-2.74 ms;
+// 500 0.73 / 1.25 ms. Chunks of 1 (5.65 ms), 8 (5.76-5.88) and 16 (6.7-7.0)
+// were slower at 10,000.
+constexpr uint32_t kLongBatch = 256;
 
 struct Feeder {
   uint32_t g;        // current part
   uint32_t visited;  // parts found used up
+  uint32_t grab;     // tasks per chunk (the same in every CTA of a launch)
 
   // Next chunk of tasks of the current part: positions [*start, *end) of
   // the part (task index = g + position * kGroups); *start == *end when no
@@ -247,7 +253,7 @@ struct Feeder {
       unsigned long long t = 0;
       uint32_t stop = 0;
       if (lane_id() == 0) {
-        t = atomicAdd(&hdr->cursor[g].next, static_cast<unsigned long long>(kGrab));
+        t = atomicAdd(&hdr->cursor[g].next, static_cast<unsigned long long>(grab));
         stop = *reinterpret_cast<volatile const unsigned int *>(&hdr->abort);
       }
       t = __shfl_sync(0xffffffffu, t, 0);
@@ -258,7 +264,7 @@ struct Feeder {
       }
       if (t < count) {
         *start = static_cast<uint32_t>(t);
-        *end = min(*start + kGrab, count);
+        *end = min(*start + grab, count);
         return;
       }
       g = (g + 1) % kGroups;
@@ -296,7 +302,8 @@ __global__ void __launch_bounds__(MAXT, MINB) batch_kernel(const __grid_constant
                                : nullptr;
   const uint32_t total = static_cast<uint32_t>(min(static_cast<uint64_t>(hdr->total), a.capacity));
   const uint32_t lane = lane_id();
-  Feeder feed{blockIdx.x % kGroups, 0};
+  Feeder feed{blockIdx.x % kGroups, 0,
+              total >= static_cast<uint64_t>(kLongBatch) * gridDim.x ? 4u : 2u};
   uint32_t cur, end;
   feed.next(hdr, total, &cur, &end);
   bool have = cur < end;
